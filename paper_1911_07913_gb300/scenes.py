@@ -1,0 +1,250 @@
+"""Seeded synthetic MPM scenes (inputs only).
+
+This module builds particle arrays, material tables and boundary-condition
+lists for the workloads the HOT step is exercised on.  It contains no part of
+the method's arithmetic: no kernel weights, no transfers, no energies.  Both
+the CUDA path and the FP64 oracle receive the arrays it returns, so the two
+sides always see bit-identical inputs.
+
+Shapes follow the paper's benchmark set (Table 2: bar-twisting scene "Twist",
+stiffness-contrast bars, soft boxes) at sizes chosen for one GPU; the paper's
+meshes are not available, so boxes and bars of the stated cell counts stand in
+for them.  Every scene is drawn from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+MODEL_FCR = 0   # fixed-corotated elasticity (Stomakhin et al. 2012), Sec. 6.1
+MODEL_NH = 1    # compressible Neo-Hookean
+
+BC_STICKY = 0   # nodes inside the box get v = 0
+BC_ROTATE = 1   # nodes inside the box get v = omega * axis x (x_i - center)
+
+
+@dataclasses.dataclass
+class Material:
+    E: float
+    nu: float
+    rho: float
+    model: int = MODEL_FCR
+    plasticity: int = 0
+    yield_stress: float = 0.0
+
+
+@dataclasses.dataclass
+class BoundaryBox:
+    type: int
+    lo: tuple
+    hi: tuple
+    axis: tuple = (0.0, 0.0, 1.0)
+    center: tuple = (0.0, 0.0, 0.0)
+    omega: float = 0.0
+
+
+@dataclasses.dataclass
+class Scene:
+    """Particle state plus grid description of one MPM scene.
+
+    Arrays are C-contiguous float64 (int32 for ``mat``):
+    x, v: (N, 3); F, C: (N, 3, 3) row-major; vol, mass: (N,); mat: (N,).
+    ``grid_dims`` counts cells per axis; nodes run 0..grid_dims inclusive.
+    """
+    x: np.ndarray
+    v: np.ndarray
+    F: np.ndarray
+    C: np.ndarray
+    vol: np.ndarray
+    mass: np.ndarray
+    mat: np.ndarray
+    materials: List[Material]
+    dx: float
+    origin: np.ndarray
+    grid_dims: np.ndarray
+    gravity: np.ndarray
+    bcs: List[BoundaryBox]
+    name: str = "scene"
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def copy(self) -> "Scene":
+        return dataclasses.replace(
+            self, x=self.x.copy(), v=self.v.copy(), F=self.F.copy(), C=self.C.copy(),
+            vol=self.vol.copy(), mass=self.mass.copy(), mat=self.mat.copy(),
+            materials=list(self.materials), origin=self.origin.copy(),
+            grid_dims=self.grid_dims.copy(), gravity=self.gravity.copy(), bcs=list(self.bcs))
+
+    def subset(self, idx: np.ndarray) -> "Scene":
+        s = self.copy()
+        for k in ("x", "v", "F", "C", "vol", "mass", "mat"):
+            setattr(s, k, np.ascontiguousarray(getattr(self, k)[idx]))
+        return s
+
+
+@dataclasses.dataclass
+class SolverOptions:
+    """Solver settings; defaults are the paper's (Sec. 6.1: 3 levels, one SGS
+    sweep, L-BFGS window 8, eps = 1e-7, CFL 0.6, 24 FPS)."""
+    eps: float = 1e-7
+    cn_mode: int = 0          # 0: characteristic norm (Sec. 5.2); 1: ||g|| <= eps ||g^1||
+    lbfgs_m: int = 8
+    levels: int = 3
+    precision: int = 0        # 0: FP64 everywhere; 1: FP32 Hessian/V-cycle
+    max_iters: int = 500
+    max_ls: int = 50
+    max_coarse_cg: int = 0    # 0: number of coarsest-level DOFs
+    dt: float = 0.0           # > 0: fixed step; else CFL rule
+    fps: float = 24.0
+    cfl: float = 0.6
+
+
+def _jittered_block(rng, cell_lo, cell_hi, dx, origin, ppc_axis=2):
+    """Particles ``ppc_axis**3`` per cell, each uniform inside its sub-cell."""
+    lo = np.asarray(cell_lo, np.int64)
+    hi = np.asarray(cell_hi, np.int64)
+    counts = (hi - lo) * ppc_axis
+    gz, gy, gx = np.meshgrid(np.arange(counts[2]), np.arange(counts[1]),
+                             np.arange(counts[0]), indexing="ij")
+    sub = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1).astype(np.float64)
+    jitter = rng.random(sub.shape)
+    x = origin + (lo + (sub + jitter) / ppc_axis) * dx
+    return np.ascontiguousarray(x)
+
+
+def _assemble(x, v, mat, materials, dx, ppc, origin, dims, gravity, bcs, name, F=None):
+    n = x.shape[0]
+    vol = np.full(n, dx ** 3 / ppc)
+    rho = np.array([materials[m].rho for m in mat])
+    mass = rho * vol
+    if F is None:
+        F = np.tile(np.eye(3), (n, 1, 1))
+    return Scene(x=np.ascontiguousarray(x, np.float64), v=np.ascontiguousarray(v, np.float64),
+                 F=np.ascontiguousarray(F, np.float64), C=np.zeros((n, 3, 3)),
+                 vol=vol, mass=mass, mat=np.ascontiguousarray(mat, np.int32),
+                 materials=materials, dx=float(dx), origin=np.asarray(origin, np.float64),
+                 grid_dims=np.asarray(dims, np.int32), gravity=np.asarray(gravity, np.float64),
+                 bcs=bcs, name=name)
+
+
+def cube_scene(seed: int = 0, res: int = 32, cube_lo=(11, 4, 11), side: int = 10,
+               E: float = 1e5, nu: float = 0.3, rho: float = 1000.0,
+               model: int = MODEL_FCR, vel_amp: float = 0.5, floor_nodes: float = 3.5,
+               gravity=(0.0, -9.8, 0.0)) -> Scene:
+    """Elastic cube with random initial velocity over a sticky floor.
+
+    Default: 10^3 cells x 8 particles = 8000 particles on a 32^3 grid,
+    dx = 1/32, FCR E = 1e5, nu = 0.3, rho = 1000, v ~ U[-0.5, 0.5]^3; the floor
+    holds every node with y <= 3.5 dx, so the cube's lowest node layer is held.
+    """
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / res
+    origin = np.zeros(3)
+    lo = np.asarray(cube_lo)
+    x = _jittered_block(rng, lo, lo + side, dx, origin)
+    v = rng.uniform(-vel_amp, vel_amp, size=x.shape)
+    mats = [Material(E, nu, rho, model)]
+    big = 1e30
+    bcs = [BoundaryBox(BC_STICKY, (-big, -big, -big), (big, floor_nodes * dx, big))]
+    return _assemble(x, v, np.zeros(x.shape[0], np.int32), mats, dx, 8, origin,
+                     (res, res, res), gravity, bcs, f"cube{side}_r{res}")
+
+
+def two_bars_scene(seed: int = 0, res: int = 256, width: int = 20, length: int = 94,
+                   gap: int = 8, E_a: float = 1e5, E_b: float = 1e9, nu: float = 0.4,
+                   rho: float = 2000.0, model: int = MODEL_NH, omega: float = 1.0,
+                   end_cells: int = 4, gravity=(0.0, -9.8, 0.0)) -> Scene:
+    """Two parallel bars along z, twisted by prescribed end rotations.
+
+    Stand-in for the paper's Twist scene (Fig. 1, Table 2: rho = 2000,
+    nu = 0.4, stiffness contrast).  Default: res 256 (dx = 1/256), bars of
+    20 x 20 x 94 cells, 8 particles per cell (601,600 particles), bar A
+    E = 1e5, bar B E = 1e9, Neo-Hookean.  The ``end_cells`` end layers of
+    each bar rotate about the bar axis at +omega (low-z end) and -omega
+    (high-z end).
+    """
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / res
+    origin = np.zeros(3)
+    c = res // 2
+    half_gap = gap // 2
+    y0, y1 = c - width // 2, c - width // 2 + width
+    z0, z1 = c - length // 2, c - length // 2 + length
+    xs = [(c - half_gap - width, c - half_gap), (c + half_gap, c + half_gap + width)]
+    mats = [Material(E_a, nu, rho, model), Material(E_b, nu, rho, model)]
+    parts, mids = [], []
+    bcs = []
+    for b, (x0, x1) in enumerate(xs):
+        xb = _jittered_block(rng, (x0, y0, z0), (x1, y1, z1), dx, origin)
+        parts.append(xb)
+        mids.append(np.full(xb.shape[0], b, np.int32))
+        center = (0.5 * (x0 + x1) * dx, 0.5 * (y0 + y1) * dx, 0.0)
+        lo_x, hi_x = (x0 - 3) * dx, (x1 + 3) * dx
+        lo_y, hi_y = (y0 - 3) * dx, (y1 + 3) * dx
+        bcs.append(BoundaryBox(BC_ROTATE, (lo_x, lo_y, (z0 - 3) * dx),
+                               (hi_x, hi_y, (z0 + end_cells + 0.5) * dx),
+                               (0.0, 0.0, 1.0), center, omega))
+        bcs.append(BoundaryBox(BC_ROTATE, (lo_x, lo_y, (z1 - end_cells - 0.5) * dx),
+                               (hi_x, hi_y, (z1 + 3) * dx),
+                               (0.0, 0.0, 1.0), center, -omega))
+    x = np.concatenate(parts)
+    mat = np.concatenate(mids)
+    v = np.zeros_like(x)
+    return _assemble(x, v, mat, mats, dx, 8, origin, (res, res, res), gravity, bcs,
+                     f"two_bars_w{width}_l{length}_r{res}")
+
+
+def two_bars_2m_scene(seed: int = 0) -> Scene:
+    """The two-bar scene at 1.5x resolution: dx = 1/384, bars 30 x 30 x 141
+    cells, 8 particles per cell (2,030,400 particles)."""
+    return two_bars_scene(seed=seed, res=384, width=30, length=141, gap=12)
+
+
+def tiny_scene(seed: int = 0, res: int = 8, cells=(2, 2, 2), lo=(3, 3, 3), ppc_axis: int = 1,
+               E: float = 1e4, nu: float = 0.3, rho: float = 1000.0, model: int = MODEL_FCR,
+               vel_amp: float = 0.3, F_jitter: float = 0.0, gravity=(0.0, -9.8, 0.0),
+               bcs: Optional[list] = None) -> Scene:
+    """A handful of particles for finite-difference and dense-solve checks."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / res
+    origin = np.zeros(3)
+    lo = np.asarray(lo)
+    x = _jittered_block(rng, lo, lo + np.asarray(cells), dx, origin, ppc_axis)
+    n = x.shape[0]
+    v = rng.uniform(-vel_amp, vel_amp, size=x.shape)
+    F = np.tile(np.eye(3), (n, 1, 1)) + F_jitter * rng.uniform(-1, 1, size=(n, 3, 3))
+    sc = _assemble(x, v, np.zeros(n, np.int32), [Material(E, nu, rho, model)], dx,
+                   ppc_axis ** 3, origin, (res, res, res), gravity, bcs or [], "tiny", F=F)
+    sc.C = rng.uniform(-vel_amp, vel_amp, size=(n, 3, 3)) * res * 0.1
+    return sc
+
+
+def stretched_box_scene(seed: int = 0, res: int = 32, side: int = 8, E: float = 1e4,
+                        nu: float = 0.3, rho: float = 1000.0) -> Scene:
+    """Soft box whose particles start with diag(F) ~ U[0.7, 1.3] (Sec. 6.3,
+    'Visualization of Convergence'); no gravity, no boundary conditions."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / res
+    origin = np.zeros(3)
+    lo = np.full(3, (res - side) // 2)
+    x = _jittered_block(rng, lo, lo + side, dx, origin)
+    n = x.shape[0]
+    F = np.zeros((n, 3, 3))
+    d = rng.uniform(0.7, 1.3, size=(n, 3))
+    F[:, 0, 0], F[:, 1, 1], F[:, 2, 2] = d[:, 0], d[:, 1], d[:, 2]
+    return _assemble(x, np.zeros_like(x), np.zeros(n, np.int32), [Material(E, nu, rho)], dx, 8,
+                     origin, (res, res, res), (0.0, 0.0, 0.0), [], f"stretched{side}", F=F)
+
+
+def scene_by_name(name: str, seed: int = 0) -> Scene:
+    if name == "cube8k":
+        return cube_scene(seed)
+    if name == "two_bars_600k":
+        return two_bars_scene(seed)
+    if name == "two_bars_2m":
+        return two_bars_2m_scene(seed)
+    raise KeyError(name)
