@@ -1,0 +1,222 @@
+/*
+ * hot_mpm.h -- C ABI of the GB300 (sm_103a) implementation of the implicit
+ * MPM time step "Hierarchical Optimization Time Integration" (HOT), Wang et
+ * al., arXiv 1911.07913.
+ *
+ * One call sequence advances one scene by one implicit-Euler step, following
+ * the operation sequence of Sec. 3.1 (P2G, grid time step, G2P, strain
+ * update, advection):
+ *
+ *     mpm_p2g(s);            bin/sort particles, APIC P2G, boundary conditions
+ *     mpm_solve_step(s, &st) minimise Eq. 1 with HOT (Alg. 3, V-cycle Alg. 2)
+ *     mpm_g2p(s);            APIC G2P, F update, advection
+ *
+ * or mpm_step() for the three.  All arithmetic runs in the library's CUDA
+ * kernels on the stream given at creation; there is no CPU fallback.
+ *
+ * Conventions
+ *   - Every function returns an mpm_status; nothing throws across the ABI.
+ *     mpm_last_error(s) returns a message for the last failure on s
+ *     (thread-local when s is NULL).
+ *   - Particle arrays are row-major AoS as a caller holds them: x, v (n x 3),
+ *     F, C (n x 3 x 3, F[p*9 + 3a + b] = F_ab), vol, mass (n), all float64;
+ *     material_id (n) int32.  "host" or "device" as the flag says.
+ *   - Grid nodes are integer triples (i, j, k), node position origin + dx*(i,j,k);
+ *     a scene's active nodes are the union of its particles' 3x3x3 quadratic
+ *     B-spline stencils, listed in (k, j, i)-lexicographic order.
+ *   - Node vectors (dv, g, b, u) are n_nodes x 3 float64, row-major.
+ *   - The library owns every device buffer it allocates; caller pointers are
+ *     only read or written during the call.
+ *   - Calls on one scene are not thread-safe; different scenes are
+ *     independent.
+ */
+#ifndef HOT_MPM_H
+#define HOT_MPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_scene *mpm_scene_t;
+
+typedef enum {
+  MPM_OK = 0,
+  MPM_ERR_INVALID_ARG = 1,   /* null pointer, bad size or option */
+  MPM_ERR_OOM = 2,           /* device allocation failed */
+  MPM_ERR_CUDA = 3,          /* a CUDA call failed (message has the code) */
+  MPM_ERR_NOT_CONVERGED = 4, /* iteration cap reached; state = last accepted iterate */
+  MPM_ERR_LINESEARCH = 5,    /* no energy decrease within max_ls halvings */
+  MPM_ERR_NUMERIC = 6,       /* NaN/Inf in a norm or energy */
+  MPM_ERR_ADMISSION = 7,     /* serving: footprint exceeds the memory budget */
+  MPM_ERR_STATE = 8,         /* call out of order (p2g -> solve -> g2p) */
+  MPM_ERR_DOMAIN = 9,        /* a particle stencil leaves the grid */
+  MPM_ERR_TIMEOUT = 10       /* a bounded device-side wait gave up */
+} mpm_status;
+
+/* Material (Sec. 6.1, Table 2).  model 0: fixed corotated (Stomakhin et al.
+ * 2012); 1: compressible Neo-Hookean.  plasticity is reserved (0). */
+typedef struct {
+  double E, nu, rho, yield_stress;
+  int32_t model;
+  int32_t plasticity;
+} mpm_material;
+
+/* Dirichlet box (Sec. 4.1: boundary conditions by projection).  A node whose
+ * position lies in [lo, hi] (inclusive, per axis) is held: type 0 prescribes
+ * v = 0, type 1 prescribes v = omega * axis x (x_i - center).  Boxes apply in
+ * list order.  Independently of the list, nodes within 3 cells of the grid
+ * walls are held at v = 0. */
+typedef struct {
+  int32_t type;
+  int32_t reserved;
+  double lo[3], hi[3], axis[3], center[3];
+  double omega;
+} mpm_bc;
+
+typedef struct {
+  int64_t n_particles;
+  const double *x, *v, *F, *C, *vol, *mass; /* see layout above; C may be NULL (= 0) */
+  const int32_t *material_id;               /* may be NULL (= material 0) */
+  const mpm_material *materials;            /* host array */
+  int32_t n_materials;
+  int32_t grid_dims[3];                     /* cells per axis; nodes 0..grid_dims */
+  double dx;
+  double origin[3];
+  double gravity[3];
+  const mpm_bc *bcs;                        /* host array, may be NULL */
+  int32_t n_bcs;
+  int32_t inputs_on_device;                 /* 1: particle arrays are device pointers */
+  void *cuda_stream;                        /* cudaStream_t, NULL = legacy default stream */
+} mpm_scene_desc;
+
+/* Solver options; the paper's settings (Sec. 6.1) are eps = 1e-7, cn_mode 0,
+ * lbfgs_m = 8, levels = 3, cfl = 0.6, fps = 24. */
+typedef struct {
+  double eps;            /* termination tolerance */
+  int32_t cn_mode;       /* 0: ||g^||_2 <= eps sqrt(n) with the node-wise CN
+                            of Sec. 5.2;  1: ||g||_2 <= eps ||g^1||_2 */
+  int32_t lbfgs_m;       /* L-BFGS window w (1..16) */
+  int32_t levels;        /* multigrid levels M (1..8) */
+  int32_t precision;     /* 0: FP64 everywhere; 1: FP32 Hessian, smoother and
+                            coarse solve, FP64 energy/gradient/L-BFGS/CN */
+  int32_t max_iters;     /* L-BFGS iteration cap */
+  int32_t max_ls;        /* line-search halvings cap */
+  int32_t max_coarse_cg; /* coarsest-level PCG cap; 0 = number of coarse DOFs */
+  int32_t record_trace;  /* 1: keep the decision trace (mpm_get_trace) */
+  double dt;             /* > 0: fixed step; else min(1/fps, cfl dx / v_max) */
+  double fps;
+  double cfl;
+} mpm_solver_opts;
+
+typedef struct {
+  int32_t iters;           /* L-BFGS iterations (Alg. 3 loop trips) */
+  int32_t ls_trials;       /* energy evaluations in line searches */
+  int32_t coarse_cg_iters; /* coarsest PCG iterations over all V-cycles */
+  int32_t vcycles;
+  double final_norm;       /* the termination norm at exit */
+  double energy;           /* E(dv) at exit, Eq. 1 without constants */
+  double dt_used;
+  int64_t n_particles;
+  int64_t n_nodes[8];      /* active nodes per multigrid level */
+  int64_t nnz_blocks[8];   /* 3x3 blocks per level */
+  int32_t n_levels;
+  int32_t status;
+} mpm_step_stats;
+
+/* Device memory hook.  alloc(bytes, stream, ctx) returns device memory or
+ * NULL; free(ptr, stream, ctx).  Default: cudaMalloc / cudaFree.  The Python
+ * binding installs PyTorch's caching allocator.  Set before creating scenes. */
+typedef void *(*mpm_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*mpm_free_fn)(void *ptr, void *stream, void *ctx);
+mpm_status mpm_set_allocator(mpm_alloc_fn alloc, mpm_free_fn free_fn, void *ctx);
+
+/* Create a scene: copies particles and settings into library-owned device
+ * memory.  Errors: INVALID_ARG (null/size/option), OOM, CUDA. */
+mpm_status mpm_create_scene(const mpm_scene_desc *desc, const mpm_solver_opts *opts,
+                            mpm_scene_t *out);
+mpm_status mpm_destroy_scene(mpm_scene_t s);
+const char *mpm_last_error(mpm_scene_t s);
+
+/* Replace the options of an existing scene (same constraints as create). */
+mpm_status mpm_set_options(mpm_scene_t s, const mpm_solver_opts *opts);
+
+/* Sec. 3.1 P2G: sort particles by cell (bit-exact cell keys), build the
+ * active node set, APIC transfer of mass and momentum, mass-weighted xi_i
+ * for the characteristic norm (Sec. 5.2), Dirichlet nodes, and the step size
+ * dt.  Errors: DOMAIN when a stencil leaves the grid. */
+mpm_status mpm_p2g(mpm_scene_t s);
+
+/* Projected Hessian at dv = 0 (Alg. 3 "projectHessian") and the Galerkin
+ * hierarchy H^{m+1} = R H^m P (Eq. "buildMultigrid").  mpm_solve_step calls
+ * it when needed; exposed for inspection.  Requires mpm_p2g. */
+mpm_status mpm_build_hierarchy(mpm_scene_t s);
+
+/* Alg. 3: minimise Eq. 1 over dv with L-BFGS (window w), the V-cycle of
+ * Alg. 2 as initial inverse Hessian, backtracking line search and the
+ * termination test of cn_mode.  The grid velocity v^{n+1} = v^n + dv stays on
+ * the device.  stats may be NULL.  Errors: NOT_CONVERGED, LINESEARCH,
+ * NUMERIC, TIMEOUT; the state then holds the last accepted iterate. */
+mpm_status mpm_solve_step(mpm_scene_t s, mpm_step_stats *stats);
+
+/* Sec. 3.1 G2P: APIC velocity and affine matrix, F_p <- (I + dt grad v) F_p,
+ * x_p <- x_p + dt v_p.  Requires a solved step. */
+mpm_status mpm_g2p(mpm_scene_t s);
+
+/* p2g + solve_step + g2p. */
+mpm_status mpm_step(mpm_scene_t s, mpm_step_stats *stats);
+
+/* Particle state in the caller's original order (any pointer may be NULL).
+ * to_device: 1 if the pointers are device memory. */
+mpm_status mpm_get_state(mpm_scene_t s, double *x, double *v, double *F, double *C,
+                         int32_t to_device);
+/* Overwrite the particle state (original order; NULL keeps a field). */
+mpm_status mpm_set_state(mpm_scene_t s, const double *x, const double *v, const double *F,
+                         const double *C, int32_t from_device);
+
+/* Grid after P2G (host pointers, any may be NULL; call with all NULL to get
+ * n_nodes): node_ijk (n x 3 int32), m (n), v (n x 3, v^n with prescribed
+ * values at held nodes), xi (n), fixed (n, 0/1), dv (n x 3, the last
+ * solution, zero before a solve). */
+mpm_status mpm_get_grid(mpm_scene_t s, int64_t *n_nodes, int32_t *node_ijk, double *m,
+                        double *v, double *xi, int32_t *fixed, double *dv);
+
+/* Eq. 1 energy and its gradient at a caller-given dv (host n x 3), using the
+ * current P2G state and dt.  Sec. 3.1 / Sec. 4.1. */
+mpm_status mpm_eval_energy(mpm_scene_t s, const double *dv, double *energy);
+mpm_status mpm_eval_gradient(mpm_scene_t s, const double *dv, double *grad);
+
+/* Level `level` of the hierarchy as block-CSR (host pointers; call with
+ * row_ptr == NULL to get sizes).  cols are node indices of that level,
+ * vals are 9 values per block, row-major 3x3, in the precision of the
+ * hierarchy converted to float64; coords (n x 3) the level's node triples. */
+mpm_status mpm_get_hessian(mpm_scene_t s, int32_t level, int64_t *n_rows, int64_t *nnz_blocks,
+                           int32_t *row_ptr, int32_t *cols, double *vals, int32_t *coords);
+
+/* One V-cycle (Alg. 2) applied to b (host n x 3) -> u; cg_iters gets the
+ * coarsest PCG count (may be NULL).  Held DOFs of b are ignored, of u zero. */
+mpm_status mpm_apply_vcycle(mpm_scene_t s, const double *b, double *u, int32_t *cg_iters);
+
+/* Decision trace of the last solve (record_trace = 1): iteration count,
+ * accepted step lengths, line-search trials, skipped L-BFGS pairs and
+ * restarts per iteration, coarse PCG counts per V-cycle.  Arrays of
+ * `capacity` entries; *n_iters and *n_vcycles get the counts. */
+mpm_status mpm_get_trace(mpm_scene_t s, int32_t capacity, int32_t *n_iters, double *alphas,
+                         int32_t *ls_trials, int32_t *skipped, int32_t *fallback,
+                         int32_t *n_vcycles, int32_t *cg_counts);
+
+/* Device bytes held by the scene (its admission footprint). */
+mpm_status mpm_scene_footprint(mpm_scene_t s, int64_t *bytes);
+
+/* Batched stepping: p2g, solve and g2p of n independent scenes.  Scenes on
+ * the same stream run back to back; scenes on different streams overlap.
+ * stats may be NULL, else n entries. */
+mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOT_MPM_H */

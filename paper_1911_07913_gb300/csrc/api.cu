@@ -1,0 +1,695 @@
+// C ABI of the HOT library (include/hot_mpm.h) and the host side of Alg. 3.
+//
+// The host issues kernels and takes the solver's scalar decisions (loop
+// termination, line-search acceptance, L-BFGS pair acceptance); every vector
+// and particle operation runs on the device.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <thread>
+
+#include "internal.h"
+
+namespace hot {
+
+static thread_local std::string g_last_error;
+static mpm_alloc_fn g_alloc = nullptr;
+static mpm_free_fn g_free = nullptr;
+static void *g_ctx = nullptr;
+
+void fail(mpm_status code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    fail(MPM_ERR_CUDA, m);
+  }
+}
+
+void *dev_alloc(size_t bytes, cudaStream_t st) {
+  void *p = nullptr;
+  if (g_alloc) {
+    p = g_alloc(bytes, (void *)st, g_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (!p) fail(MPM_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  return p;
+}
+
+void dev_free(void *p, cudaStream_t st) {
+  if (!p) return;
+  if (g_free) g_free(p, (void *)st, g_ctx);
+  else cudaFree(p);
+}
+
+int read_errflag(Scene &s) {
+  int e = 0;
+  HOT_CUDA(cudaMemcpyAsync(&e, s.errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  return e;
+}
+
+size_t Scene::bytes() const {
+  size_t b = pd.bytes() + pd_alt.bytes() + pmat.bytes() + pmat_alt.bytes() + pid.bytes() + pid_alt.bytes() +
+             mat_table.bytes() + bc_dev.bytes() + key.bytes() + slot.bytes() + perm.bytes() + tmp.bytes() +
+             cell_count.bytes() + cell_start.bytes() + cell_first.bytes() + cell_n.bytes() + cell_key.bytes() +
+             blk_first.bytes() + blk_end.bytes() + blk_key.bytes() + flags.bytes() + flag_scan.bytes() + m.bytes() +
+             v.bytes() + xi.bytes() + fixed.bytes() + mv.bytes() + mxi.bytes() + dv.bytes() + g.bytes() +
+             pdir.bytes() + q.bytes() + g_new.bytes() + dv_new.bytes() + vtmp.bytes() + hist_s.bytes() +
+             hist_y.bytes() + Lv.bytes() + Lp.bytes() + Le.bytes() + dv_e.bytes() + g_e.bytes() + part.bytes() +
+             scal.bytes() + errflag.bytes() + scan.block_sums.bytes() + scan.total.bytes() + hd.bytes() + hf.bytes();
+  for (auto &t : topo) b += t.bytes();
+  return b;
+}
+
+void Scene::release() {
+  for (auto *b : {&pd, &pd_alt, &m, &v, &xi, &mv, &mxi, &dv, &g, &pdir, &q, &g_new, &dv_new, &vtmp, &hist_s,
+                  &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e})
+    b->release();
+  for (auto *b : {&pmat, &pmat_alt, &pid, &pid_alt, &slot, &perm, &tmp, &cell_count, &cell_start, &cell_first,
+                  &cell_n, &cell_key, &blk_first, &blk_end, &blk_key, &flags, &flag_scan, &errflag})
+    b->release();
+  key.release();
+  fixed.release();
+  mat_table.release();
+  bc_dev.release();
+  scan.block_sums.release();
+  scan.total.release();
+  for (auto &t : topo) t.release();
+  hd.release();
+  hf.release();
+}
+
+namespace {
+
+void validate_opts(const mpm_solver_opts *o) {
+  if (!o) fail(MPM_ERR_INVALID_ARG, "opts is NULL");
+  if (!(o->eps > 0.0)) fail(MPM_ERR_INVALID_ARG, "eps must be > 0");
+  if (o->cn_mode != 0 && o->cn_mode != 1) fail(MPM_ERR_INVALID_ARG, "cn_mode must be 0 or 1");
+  if (o->lbfgs_m < 1 || o->lbfgs_m > MAX_HIST) fail(MPM_ERR_INVALID_ARG, "lbfgs_m must be in 1..16");
+  if (o->levels < 1 || o->levels > MAX_LEVELS) fail(MPM_ERR_INVALID_ARG, "levels must be in 1..8");
+  if (o->precision != 0 && o->precision != 1) fail(MPM_ERR_INVALID_ARG, "precision must be 0 or 1");
+  if (o->max_iters < 1 || o->max_ls < 1) fail(MPM_ERR_INVALID_ARG, "max_iters and max_ls must be >= 1");
+  if (o->max_coarse_cg < 0) fail(MPM_ERR_INVALID_ARG, "max_coarse_cg must be >= 0");
+  if (o->dt <= 0.0 && !(o->fps > 0.0 && o->cfl > 0.0)) fail(MPM_ERR_INVALID_ARG, "need dt > 0 or fps, cfl > 0");
+}
+
+void compute_dt(Scene &s) {
+  if (s.opts.dt > 0.0) {
+    s.dt = s.opts.dt;
+    return;
+  }
+  double vmax = s.np ? max_particle_speed(s) : 0.0;
+  double dt = 1.0 / s.opts.fps;
+  if (vmax > 0.0) dt = std::min(dt, s.opts.cfl * s.geo.dx / vmax);
+  s.dt = dt;
+}
+
+void do_p2g(Scene &s) {
+  HOT_CUDA(cudaMemsetAsync(s.errflag.p, 0, sizeof(int), s.st));
+  compute_dt(s);
+  if (s.np > 0) {
+    bin_and_sort(s);
+    int e = read_errflag(s);
+    if (e & DEV_ERR_DOMAIN) fail(MPM_ERR_DOMAIN, "a particle stencil leaves the grid (3 cells from the walls)");
+  } else {
+    s.n_cells = s.n_blocks = 0;
+  }
+  build_level0_nodes(s);
+  p2g_transfer(s);
+  s.nlev = 0;
+  s.phase = PH_P2G;
+  s.has_grid = true;
+  s.has_solution = false;
+}
+
+template <class T>
+void build_hier(Scene &s, Hier<T> &h) {
+  const int64_t n = s.nn();
+  s.Lv.ensure(9 * (size_t)s.np + 9);
+  velocity_gradient(s, s.v.p, nullptr, s.Lv.p);      // F at dv = 0
+  build_pattern0(s);
+  build_colors(s, 0);
+  particle_stiffness<T>(s, h);
+  hessian_assemble<T>(s, h);
+  finalize_values<T>(s, h, 0);
+  int M = 1;
+  for (int m = 0; m + 1 < s.opts.levels; ++m) {
+    build_coarse_topology(s, m);
+    build_colors(s, m + 1);
+    rap<T>(s, h, m);
+    finalize_values<T>(s, h, m + 1);
+    M = m + 2;
+  }
+  s.nlev = M;
+  (void)n;
+}
+
+void do_build(Scene &s) {
+  if (s.phase < PH_P2G) fail(MPM_ERR_STATE, "mpm_p2g must run before the hierarchy is built");
+  if (s.opts.precision == 0) build_hier<double>(s, s.hd);
+  else build_hier<float>(s, s.hf);
+  s.phase = PH_HIER;
+}
+
+int run_vcycle(Scene &s, const double *b, double *u) {
+  int its = s.opts.precision == 0 ? vcycle<double>(s, s.hd, b, u, -1) : vcycle<float>(s, s.hf, b, u, -1);
+  s.trace.cg_counts.push_back(its);
+  return its;
+}
+
+mpm_status do_solve(Scene &s, mpm_step_stats *st) {
+  if (s.phase < PH_P2G) fail(MPM_ERR_STATE, "mpm_p2g must run before mpm_solve_step");
+  if (s.phase < PH_HIER) do_build(s);
+  const int64_t n = s.nn(), n3 = 3 * n;
+  const int w = s.opts.lbfgs_m;
+  for (auto *b : {&s.dv, &s.g, &s.pdir, &s.q, &s.g_new, &s.dv_new, &s.vtmp}) b->ensure(n3 + 3);
+  s.hist_s.ensure((size_t)w * n3 + 3);
+  s.hist_y.ensure((size_t)w * n3 + 3);
+  s.Lv.ensure(9 * (size_t)s.np + 9);
+  s.Lp.ensure(9 * (size_t)s.np + 9);
+  HOT_CUDA(cudaMemsetAsync(s.dv.p, 0, sizeof(double) * n3, s.st));
+  HOT_CUDA(cudaMemsetAsync(s.errflag.p, 0, sizeof(int), s.st));
+  velocity_gradient(s, s.v.p, nullptr, s.Lv.p);
+  s.trace.clear();
+  s.hist_n = 0;
+  s.hist_head = 0;
+  const int64_t nfree = count_free(s);
+  double norms[2];
+  gradient(s, s.Lv.p, s.dv.p, s.g.p, norms);
+  const double g1n = std::sqrt(norms[0]);
+  double E = energy(s, s.Lv.p, nullptr, 0.0, s.dv.p, nullptr);
+  mpm_status status = MPM_OK;
+  int it = 0, trials_total = 0, cg_total = 0;
+  double nrm = 0.0;
+  while (true) {
+    if (!std::isfinite(norms[0]) || !std::isfinite(norms[1]) || !std::isfinite(E)) {
+      status = MPM_ERR_NUMERIC;
+      break;
+    }
+    bool done;
+    if (s.opts.cn_mode == 0) {
+      nrm = std::sqrt(norms[1]);
+      done = nrm <= s.opts.eps * std::sqrt((double)nfree);
+    } else {
+      nrm = std::sqrt(norms[0]);
+      done = nrm <= s.opts.eps * g1n;
+    }
+    if (done) break;
+    if (it >= s.opts.max_iters) {
+      status = MPM_ERR_NOT_CONVERGED;
+      break;
+    }
+    // two-loop recursion around the V-cycle initializer (Alg. 3)
+    scale_copy(s, s.q.p, -1.0, s.g.p, n3);
+    two_loop_first(s, s.q.p, n3);
+    cg_total += run_vcycle(s, s.q.p, s.pdir.p);
+    two_loop_second(s, s.pdir.p, n3);
+    int fb = 0;
+    if (dot(s, s.pdir.p, s.g.p, n3) >= 0.0) {
+      // not a descent direction: drop the history, use the V-cycle alone
+      fb = 1;
+      s.hist_n = 0;
+      scale_copy(s, s.q.p, -1.0, s.g.p, n3);
+      cg_total += run_vcycle(s, s.q.p, s.pdir.p);
+    }
+    s.trace.fallback.push_back(fb);
+    // backtracking line search on E(dv + alpha p)
+    velocity_gradient(s, s.pdir.p, nullptr, s.Lp.p);
+    double alpha = 1.0, E1 = E;
+    int t = 0;
+    bool ok = false;
+    for (t = 1; t <= s.opts.max_ls; ++t) {
+      E1 = energy(s, s.Lv.p, s.Lp.p, alpha, s.dv.p, s.pdir.p);
+      if (E1 <= E) {
+        ok = true;
+        break;
+      }
+      alpha *= 0.5;
+    }
+    trials_total += ok ? t : s.opts.max_ls;
+    if (!ok) {
+      status = MPM_ERR_LINESEARCH;
+      break;
+    }
+    s.trace.alphas.push_back(alpha);
+    s.trace.ls_trials.push_back(t);
+    const int slot = s.hist_head;
+    double *sv = s.hist_s.p + (size_t)slot * n3;
+    double *yv = s.hist_y.p + (size_t)slot * n3;
+    lincomb(s, s.dv_new.p, 1.0, s.dv.p, alpha, s.pdir.p, n3);
+    lincomb(s, sv, 1.0, s.dv_new.p, -1.0, s.dv.p, n3);
+    axpy(s, s.Lv.p, alpha, s.Lp.p, 9 * s.np);
+    std::swap(s.dv, s.dv_new);
+    gradient(s, s.Lv.p, s.dv.p, s.g_new.p, norms);
+    lincomb(s, yv, 1.0, s.g_new.p, -1.0, s.g.p, n3);
+    double d3[3];
+    dots3(s, yv, sv, n3, d3);   // y.s, y.y, s.s
+    int skip = !(d3[0] > 1e-14 * std::sqrt(d3[1] * d3[2]));
+    s.trace.skipped.push_back(skip);
+    if (!skip) {
+      s.hist_rho[slot] = 1.0 / d3[0];
+      s.hist_head = (s.hist_head + 1) % w;
+      s.hist_n = std::min(s.hist_n + 1, w);
+    }
+    std::swap(s.g, s.g_new);
+    E = E1;
+    ++it;
+  }
+  int e = read_errflag(s);
+  if (e & DEV_ERR_TIMEOUT) status = MPM_ERR_TIMEOUT;
+  s.trace.iters = it;
+  s.phase = PH_SOLVED;
+  s.has_solution = true;
+  mpm_step_stats out;
+  std::memset(&out, 0, sizeof(out));
+  out.iters = it;
+  out.ls_trials = trials_total;
+  out.coarse_cg_iters = cg_total;
+  out.vcycles = (int)s.trace.cg_counts.size();
+  out.final_norm = nrm;
+  out.energy = E;
+  out.dt_used = s.dt;
+  out.n_particles = s.np;
+  out.n_levels = s.nlev;
+  for (int m = 0; m < s.nlev && m < 8; ++m) {
+    out.n_nodes[m] = s.topo[m].n;
+    out.nnz_blocks[m] = s.topo[m].nnzb;
+  }
+  out.status = status;
+  s.last_stats = out;
+  if (st) *st = out;
+  return status;
+}
+
+void do_g2p(Scene &s) {
+  if (s.phase != PH_SOLVED) fail(MPM_ERR_STATE, "mpm_g2p needs a solved step");
+  const int64_t n3 = 3 * s.nn();
+  s.vtmp.ensure(n3 + 3);
+  lincomb(s, s.vtmp.p, 1.0, s.v.p, 1.0, s.dv.p, n3);
+  g2p_transfer(s, s.vtmp.p);
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  s.phase = PH_IDLE;
+}
+
+template <class F>
+mpm_status guarded(Scene *s, F &&f) {
+  try {
+    return f();
+  } catch (const Error &e) {
+    if (s) s->last_error = e.msg;
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::exception &e) {
+    if (s) s->last_error = e.what();
+    g_last_error = e.what();
+    return MPM_ERR_INVALID_ARG;
+  }
+}
+
+template <class T>
+void hier_to_host(Scene &s, Hier<T> &h, int level, double *vals) {
+  Topo &t = s.topo[level];
+  std::vector<T> hv(9 * (size_t)t.nnzb);
+  std::vector<int> rp(t.n + 1);
+  HOT_CUDA(cudaMemcpyAsync(hv.data(), h.L[level].vals.p, sizeof(T) * hv.size(), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaMemcpyAsync(rp.data(), t.row_ptr.p, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  for (int64_t i = 0; i < t.n; ++i) {
+    int b0 = rp[i], nb = rp[i + 1] - rp[i];
+    for (int k = 0; k < nb; ++k)
+      for (int e = 0; e < 9; ++e) vals[9 * (size_t)(b0 + k) + e] = (double)hv[9 * (size_t)b0 + (size_t)e * nb + k];
+  }
+}
+
+}  // namespace
+}  // namespace hot
+
+using namespace hot;
+
+extern "C" {
+
+mpm_status mpm_set_allocator(mpm_alloc_fn alloc, mpm_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) {
+    g_last_error = "alloc and free must both be set or both be NULL";
+    return MPM_ERR_INVALID_ARG;
+  }
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_ctx = ctx;
+  return MPM_OK;
+}
+
+const char *mpm_last_error(mpm_scene_t s) {
+  if (s) return reinterpret_cast<Scene *>(s)->last_error.c_str();
+  return g_last_error.c_str();
+}
+
+mpm_status mpm_create_scene(const mpm_scene_desc *d, const mpm_solver_opts *o, mpm_scene_t *out) {
+  return guarded(nullptr, [&]() -> mpm_status {
+    if (!d || !out) fail(MPM_ERR_INVALID_ARG, "desc and out must not be NULL");
+    *out = nullptr;
+    validate_opts(o);
+    if (d->n_particles < 0 || d->n_particles > (int64_t)INT32_MAX / 2) fail(MPM_ERR_INVALID_ARG, "bad n_particles");
+    const int64_t np = d->n_particles;
+    if (np > 0 && (!d->x || !d->v || !d->F || !d->vol || !d->mass))
+      fail(MPM_ERR_INVALID_ARG, "x, v, F, vol and mass are required");
+    if (d->n_materials < 1 || !d->materials) fail(MPM_ERR_INVALID_ARG, "at least one material is required");
+    if (d->n_bcs < 0 || (d->n_bcs > 0 && !d->bcs)) fail(MPM_ERR_INVALID_ARG, "bad bcs");
+    if (!(d->dx > 0.0)) fail(MPM_ERR_INVALID_ARG, "dx must be > 0");
+    for (int k = 0; k < 3; ++k)
+      if (d->grid_dims[k] < 8 || d->grid_dims[k] > 4096) fail(MPM_ERR_INVALID_ARG, "grid_dims must be in 8..4096");
+    for (int k = 0; k < d->n_materials; ++k) {
+      const mpm_material &m = d->materials[k];
+      if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || (m.model != 0 && m.model != 1))
+        fail(MPM_ERR_INVALID_ARG, "bad material " + std::to_string(k));
+    }
+    Scene *s = new Scene();
+    try {
+      s->np = np;
+      s->opts = *o;
+      s->mats.assign(d->materials, d->materials + d->n_materials);
+      if (d->n_bcs > 0) s->bcs.assign(d->bcs, d->bcs + d->n_bcs);
+      s->geo.dx = d->dx;
+      s->geo.inv_dx = 1.0 / d->dx;
+      for (int k = 0; k < 3; ++k) {
+        s->geo.dims[k] = d->grid_dims[k];
+        s->geo.origin[k] = d->origin[k];
+        s->geo.nb[k] = (d->grid_dims[k] + 3) / 4;
+        s->gravity[k] = d->gravity[k];
+      }
+      s->ncell_dense = (int64_t)s->geo.nb[0] * s->geo.nb[1] * s->geo.nb[2] * 64;
+      s->set_stream((cudaStream_t)d->cuda_stream);
+      int dev = 0;
+      HOT_CUDA(cudaGetDevice(&dev));
+      HOT_CUDA(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev));
+      std::vector<MatParams> mt(d->n_materials);
+      for (int k = 0; k < d->n_materials; ++k) {
+        double E = d->materials[k].E, nu = d->materials[k].nu;
+        mt[k].mu = E / (2.0 * (1.0 + nu));
+        mt[k].lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+        mt[k].xi = std::sqrt(3.0 * (2.0 * mt[k].mu + mt[k].lam) * (2.0 * mt[k].mu + mt[k].lam) +
+                             6.0 * mt[k].lam * mt[k].lam);
+        mt[k].model = d->materials[k].model;
+        mt[k].pad = 0;
+      }
+      s->mat_table.ensure(mt.size(), 1.0);
+      HOT_CUDA(cudaMemcpyAsync(s->mat_table.p, mt.data(), sizeof(MatParams) * mt.size(), cudaMemcpyHostToDevice, s->st));
+      s->bc_dev.ensure(std::max<size_t>(1, s->bcs.size()), 1.0);
+      if (!s->bcs.empty())
+        HOT_CUDA(cudaMemcpyAsync(s->bc_dev.p, s->bcs.data(), sizeof(mpm_bc) * s->bcs.size(), cudaMemcpyHostToDevice,
+                                 s->st));
+      s->errflag.ensure(4, 1.0);
+      HOT_CUDA(cudaMemsetAsync(s->errflag.p, 0, sizeof(int) * 4, s->st));
+      s->pd.ensure((size_t)PF_COUNT * np + 1, 1.0);
+      s->pmat.ensure(np + 1, 1.0);
+      s->pid.ensure(np + 1, 1.0);
+      if (np > 0) {
+        std::vector<int> ids(np);
+        for (int64_t i = 0; i < np; ++i) ids[i] = (int)i;
+        HOT_CUDA(cudaMemcpyAsync(s->pid.p, ids.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s->st));
+        cudaMemcpyKind kind = d->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        HOT_CUDA(cudaMemsetAsync(s->pd.p + (size_t)PF_C * np, 0, sizeof(double) * 9 * np, s->st));
+        HOT_CUDA(cudaMemcpyAsync(s->pd.p + (size_t)PF_VOL * np, d->vol, sizeof(double) * np, kind, s->st));
+        HOT_CUDA(cudaMemcpyAsync(s->pd.p + (size_t)PF_MASS * np, d->mass, sizeof(double) * np, kind, s->st));
+        if (d->material_id) {
+          if (!d->inputs_on_device) {
+            for (int64_t i = 0; i < np; ++i)
+              if (d->material_id[i] < 0 || d->material_id[i] >= d->n_materials)
+                fail(MPM_ERR_INVALID_ARG, "material_id out of range");
+          }
+          HOT_CUDA(cudaMemcpyAsync(s->pmat.p, d->material_id, sizeof(int) * np, kind, s->st));
+        } else {
+          HOT_CUDA(cudaMemsetAsync(s->pmat.p, 0, sizeof(int) * np, s->st));
+        }
+        load_state_from_user_order(*s, d->x, d->v, d->F, d->C, d->inputs_on_device != 0);
+      }
+      HOT_CUDA(cudaStreamSynchronize(s->st));
+    } catch (...) {
+      s->release();
+      delete s;
+      throw;
+    }
+    *out = reinterpret_cast<mpm_scene_t>(s);
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_destroy_scene(mpm_scene_t sc) {
+  if (!sc) return MPM_OK;
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  cudaStreamSynchronize(s->st);
+  s->release();
+  delete s;
+  return MPM_OK;
+}
+
+mpm_status mpm_set_options(mpm_scene_t sc, const mpm_solver_opts *o) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    validate_opts(o);
+    bool rebuild = o->precision != s->opts.precision || o->levels != s->opts.levels;
+    s->opts = *o;
+    if (rebuild && s->phase >= PH_HIER) s->phase = PH_P2G;
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_p2g(mpm_scene_t sc) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    do_p2g(*s);
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_build_hierarchy(mpm_scene_t sc) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    do_build(*s);
+    HOT_CUDA(cudaStreamSynchronize(s->st));
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_solve_step(mpm_scene_t sc, mpm_step_stats *st) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    mpm_status r = do_solve(*s, st);
+    if (r != MPM_OK) s->last_error = "solve ended with status " + std::to_string((int)r);
+    return r;
+  });
+}
+
+mpm_status mpm_g2p(mpm_scene_t sc) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    do_g2p(*s);
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_step(mpm_scene_t sc, mpm_step_stats *st) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    do_p2g(*s);
+    mpm_status r = do_solve(*s, st);
+    if (r == MPM_OK || r == MPM_ERR_NOT_CONVERGED || r == MPM_ERR_LINESEARCH) do_g2p(*s);
+    if (r != MPM_OK) s->last_error = "solve ended with status " + std::to_string((int)r);
+    return r;
+  });
+}
+
+mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats) {
+  if (n < 0 || (n > 0 && !scenes)) {
+    g_last_error = "bad batch";
+    return MPM_ERR_INVALID_ARG;
+  }
+  std::vector<mpm_status> res(n, MPM_OK);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i]() {
+      cudaSetDevice(dev);
+      res[i] = mpm_step(scenes[i], stats ? &stats[i] : nullptr);
+    });
+  for (auto &t : th) t.join();
+  for (int i = 0; i < n; ++i)
+    if (res[i] != MPM_OK) return res[i];
+  return MPM_OK;
+}
+
+mpm_status mpm_get_state(mpm_scene_t sc, double *x, double *v, double *F, double *C, int32_t to_device) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    scatter_state_to_user_order(*s, x, v, F, C, to_device != 0);
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_set_state(mpm_scene_t sc, const double *x, const double *v, const double *F, const double *C,
+                         int32_t from_device) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    load_state_from_user_order(*s, x, v, F, C, from_device != 0);
+    s->phase = PH_IDLE;
+    s->has_grid = s->has_solution = false;
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_get_grid(mpm_scene_t sc, int64_t *n_nodes, int32_t *node_ijk, double *m, double *v, double *xi,
+                        int32_t *fixed, double *dv) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    if (!s->has_grid && (node_ijk || m || v || xi || fixed || dv)) fail(MPM_ERR_STATE, "no grid before mpm_p2g");
+    const int64_t n = s->has_grid ? s->nn() : 0;
+    if (n_nodes) *n_nodes = n;
+    if (n == 0) return MPM_OK;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+      HOT_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->st));
+    };
+    if (node_ijk) cp(node_ijk, s->topo[0].coords.p, sizeof(int) * 3 * n);
+    if (m) cp(m, s->m.p, sizeof(double) * n);
+    if (v) cp(v, s->v.p, sizeof(double) * 3 * n);
+    if (xi) cp(xi, s->xi.p, sizeof(double) * n);
+    std::vector<uint8_t> fx;
+    if (fixed) {
+      fx.resize(n);
+      cp(fx.data(), s->fixed.p, n);
+    }
+    if (dv) {
+      if (s->has_solution) cp(dv, s->dv.p, sizeof(double) * 3 * n);
+      else std::memset(dv, 0, sizeof(double) * 3 * n);
+    }
+    HOT_CUDA(cudaStreamSynchronize(s->st));
+    if (fixed)
+      for (int64_t i = 0; i < n; ++i) fixed[i] = fx[i];
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_eval_energy(mpm_scene_t sc, const double *dvh, double *E) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s || !dvh || !E) fail(MPM_ERR_INVALID_ARG, "NULL argument");
+    if (s->phase < PH_P2G) fail(MPM_ERR_STATE, "mpm_p2g must run first");
+    const int64_t n3 = 3 * s->nn();
+    s->dv_e.ensure(n3 + 3);
+    s->Le.ensure(9 * (size_t)s->np + 9);
+    HOT_CUDA(cudaMemcpyAsync(s->dv_e.p, dvh, sizeof(double) * n3, cudaMemcpyHostToDevice, s->st));
+    velocity_gradient(*s, s->v.p, s->dv_e.p, s->Le.p);
+    *E = energy(*s, s->Le.p, nullptr, 0.0, s->dv_e.p, nullptr);
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_eval_gradient(mpm_scene_t sc, const double *dvh, double *gh) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s || !dvh || !gh) fail(MPM_ERR_INVALID_ARG, "NULL argument");
+    if (s->phase < PH_P2G) fail(MPM_ERR_STATE, "mpm_p2g must run first");
+    const int64_t n3 = 3 * s->nn();
+    s->dv_e.ensure(n3 + 3);
+    s->g_e.ensure(n3 + 3);
+    s->Le.ensure(9 * (size_t)s->np + 9);
+    HOT_CUDA(cudaMemcpyAsync(s->dv_e.p, dvh, sizeof(double) * n3, cudaMemcpyHostToDevice, s->st));
+    velocity_gradient(*s, s->v.p, s->dv_e.p, s->Le.p);
+    double norms[2];
+    gradient(*s, s->Le.p, s->dv_e.p, s->g_e.p, norms);
+    HOT_CUDA(cudaMemcpyAsync(gh, s->g_e.p, sizeof(double) * n3, cudaMemcpyDeviceToHost, s->st));
+    HOT_CUDA(cudaStreamSynchronize(s->st));
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_get_hessian(mpm_scene_t sc, int32_t level, int64_t *n_rows, int64_t *nnz_blocks, int32_t *row_ptr,
+                           int32_t *cols, double *vals, int32_t *coords) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    if (s->phase < PH_HIER) fail(MPM_ERR_STATE, "no hierarchy: call mpm_build_hierarchy or mpm_solve_step");
+    if (level < 0 || level >= s->nlev) fail(MPM_ERR_INVALID_ARG, "level out of range");
+    Topo &t = s->topo[level];
+    if (n_rows) *n_rows = t.n;
+    if (nnz_blocks) *nnz_blocks = t.nnzb;
+    if (row_ptr) HOT_CUDA(cudaMemcpyAsync(row_ptr, t.row_ptr.p, sizeof(int) * (t.n + 1), cudaMemcpyDeviceToHost, s->st));
+    if (cols) HOT_CUDA(cudaMemcpyAsync(cols, t.cols.p, sizeof(int) * t.nnzb, cudaMemcpyDeviceToHost, s->st));
+    if (coords) HOT_CUDA(cudaMemcpyAsync(coords, t.coords.p, sizeof(int) * 3 * t.n, cudaMemcpyDeviceToHost, s->st));
+    HOT_CUDA(cudaStreamSynchronize(s->st));
+    if (vals) {
+      if (s->opts.precision == 0) hier_to_host<double>(*s, s->hd, level, vals);
+      else hier_to_host<float>(*s, s->hf, level, vals);
+    }
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_apply_vcycle(mpm_scene_t sc, const double *b, double *u, int32_t *cg_iters) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s || !b || !u) fail(MPM_ERR_INVALID_ARG, "NULL argument");
+    if (s->phase < PH_HIER) fail(MPM_ERR_STATE, "no hierarchy: call mpm_build_hierarchy first");
+    const int64_t n3 = 3 * s->nn();
+    s->dv_e.ensure(n3 + 3);
+    s->g_e.ensure(n3 + 3);
+    HOT_CUDA(cudaMemsetAsync(s->errflag.p, 0, sizeof(int), s->st));
+    HOT_CUDA(cudaMemcpyAsync(s->dv_e.p, b, sizeof(double) * n3, cudaMemcpyHostToDevice, s->st));
+    int its = s->opts.precision == 0 ? vcycle<double>(*s, s->hd, s->dv_e.p, s->g_e.p, -1)
+                                     : vcycle<float>(*s, s->hf, s->dv_e.p, s->g_e.p, -1);
+    HOT_CUDA(cudaMemcpyAsync(u, s->g_e.p, sizeof(double) * n3, cudaMemcpyDeviceToHost, s->st));
+    HOT_CUDA(cudaStreamSynchronize(s->st));
+    if (cg_iters) *cg_iters = its;
+    if (read_errflag(*s) & DEV_ERR_TIMEOUT) fail(MPM_ERR_TIMEOUT, "coarse solve barrier timed out");
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_get_trace(mpm_scene_t sc, int32_t capacity, int32_t *n_iters, double *alphas, int32_t *ls_trials,
+                         int32_t *skipped, int32_t *fallback, int32_t *n_vcycles, int32_t *cg_counts) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    const Trace &t = s->trace;
+    if (n_iters) *n_iters = t.iters;
+    if (n_vcycles) *n_vcycles = (int)t.cg_counts.size();
+    int ni = std::min<int>(capacity, (int)t.alphas.size());
+    for (int i = 0; i < ni; ++i) {
+      if (alphas) alphas[i] = t.alphas[i];
+      if (ls_trials) ls_trials[i] = t.ls_trials[i];
+    }
+    int nf = std::min<int>(capacity, (int)t.fallback.size());
+    for (int i = 0; i < nf; ++i)
+      if (fallback) fallback[i] = t.fallback[i];
+    int ns = std::min<int>(capacity, (int)t.skipped.size());
+    for (int i = 0; i < ns; ++i)
+      if (skipped) skipped[i] = t.skipped[i];
+    int nc = std::min<int>(capacity, (int)t.cg_counts.size());
+    for (int i = 0; i < nc; ++i)
+      if (cg_counts) cg_counts[i] = t.cg_counts[i];
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_scene_footprint(mpm_scene_t sc, int64_t *bytes) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  if (!s || !bytes) return MPM_ERR_INVALID_ARG;
+  *bytes = (int64_t)s->bytes();
+  return MPM_OK;
+}
+
+}  // extern "C"

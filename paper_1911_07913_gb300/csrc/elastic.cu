@@ -1,0 +1,456 @@
+// Eq. 1 incremental potential: per-particle velocity gradients, energy,
+// gradient (the nodal force of Sec. 4.1), projected per-particle stiffness
+// and the cell-wise assembly of the fine-level 3x3-block Hessian.
+#include "internal.h"
+
+namespace hot {
+
+namespace {
+constexpr int NT = 256;
+
+struct G {
+  int dims[3], nb[3], nd[3];
+  double dx, inv_dx, o[3];
+};
+G geo(const Scene &s) {
+  G g;
+  for (int k = 0; k < 3; ++k) {
+    g.dims[k] = s.geo.dims[k];
+    g.nb[k] = s.geo.nb[k];
+    g.nd[k] = s.geo.dims[k] + 1;
+    g.o[k] = s.geo.origin[k];
+  }
+  g.dx = s.geo.dx;
+  g.inv_dx = s.geo.inv_dx;
+  return g;
+}
+
+__device__ __forceinline__ int64_t nlin(int x, int y, int z, const int *nd) {
+  return ((int64_t)z * nd[1] + y) * nd[0] + x;
+}
+
+// stencil of particle p: base node, per-axis weights and derivatives
+__device__ __forceinline__ void stencil(const double *pd, int64_t np, int64_t p, const G &g, int b[3],
+                                        double fx[3], double w[3][3], double dw[3][3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    b[k] = clampi(base_axis(pd[(PF_X + k) * np + p], g.o[k], g.inv_dx, &fx[k]), 0, g.dims[k] - 2);
+    bspline_axis<double>(fx[k], g.inv_dx, w[k], dw[k]);
+  }
+}
+
+// L_p = sum_i u_i grad w_ip^T (u2 added when present)
+__global__ void k_velgrad(const double *__restrict__ pd, int64_t np, G g, const int *__restrict__ map,
+                          const double *__restrict__ u, const double *__restrict__ u2, double *__restrict__ L) {
+  int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (p >= np) return;
+  int b[3];
+  double fx[3], w[3][3], dw[3][3];
+  stencil(pd, np, p, g, b, fx, w, dw);
+  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        int idx = map[nlin(b[0] + kx, b[1] + ky, b[2] + kz, g.nd)];
+        double ui[3] = {u[3 * idx], u[3 * idx + 1], u[3 * idx + 2]};
+        if (u2) {
+          ui[0] += u2[3 * idx];
+          ui[1] += u2[3 * idx + 1];
+          ui[2] += u2[3 * idx + 2];
+        }
+        double gw[3] = {dw[0][kx] * w[1][ky] * w[2][kz], w[0][kx] * dw[1][ky] * w[2][kz],
+                        w[0][kx] * w[1][ky] * dw[2][kz]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[3 * a + c] += ui[a] * gw[c];
+      }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) L[k * np + p] = acc[k];
+}
+
+// F = (I + dt (Lv + alpha Lp)) F^n
+__device__ __forceinline__ void deformed(const double *pd, int64_t np, int64_t p, const double *Lv,
+                                         const double *Lp, double alpha, double dt, double F[9]) {
+  double M[9], Fn[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    M[k] = Lv[k * np + p];
+    if (Lp) M[k] += alpha * Lp[k * np + p];
+    Fn[k] = pd[(PF_F + k) * np + p];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      F[3 * a + c] = Fn[3 * a + c] + dt * (M[3 * a] * Fn[c] + M[3 * a + 1] * Fn[3 + c] + M[3 * a + 2] * Fn[6 + c]);
+}
+
+// blocks [0, nbp): particle energies V_p psi(F_p); blocks [nbp, nbp+nbn): node
+// terms 1/2 m |dv + a p|^2 - dt m g.(dv + a p).  One partial per block.
+__global__ void k_energy(const double *__restrict__ pd, const int *__restrict__ pmat, const MatParams *__restrict__ mt,
+                         int64_t np, const double *__restrict__ Lv, const double *__restrict__ Lp, double alpha,
+                         double dt, int nbp, int64_t nn, const double *__restrict__ m, const double *__restrict__ dv,
+                         const double *__restrict__ pdir, double g0, double g1, double g2,
+                         double *__restrict__ part) {
+  __shared__ double sh[NT];
+  double acc = 0.0;
+  if ((int)blockIdx.x < nbp) {
+    for (int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x; p < np; p += (int64_t)nbp * NT) {
+      double F[9];
+      deformed(pd, np, p, Lv, Lp, alpha, dt, F);
+      const MatParams mp = mt[pmat[p]];
+      acc += pd[PF_VOL * np + p] * psi_density<double>(F, mp.mu, mp.lam, mp.model);
+    }
+  } else {
+    int nbn = gridDim.x - nbp;
+    for (int64_t i = (int64_t)(blockIdx.x - nbp) * NT + threadIdx.x; i < nn; i += (int64_t)nbn * NT) {
+      double d0 = dv[3 * i], d1 = dv[3 * i + 1], d2 = dv[3 * i + 2];
+      if (pdir) {
+        d0 += alpha * pdir[3 * i];
+        d1 += alpha * pdir[3 * i + 1];
+        d2 += alpha * pdir[3 * i + 2];
+      }
+      double mi = m[i];
+      acc += 0.5 * mi * (d0 * d0 + d1 * d1 + d2 * d2) - dt * mi * (g0 * d0 + g1 * d1 + g2 * d2);
+    }
+  }
+  double t = block_sum<NT>(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// gradient scatter: dt V_p P(F_p) F^n_p^T grad w_ip, one CTA per 4^3-cell block
+constexpr int NB6 = 216;
+__global__ void __launch_bounds__(NT) k_grad_scatter(const double *__restrict__ pd, const int *__restrict__ pmat,
+                                                     const MatParams *__restrict__ mt, int64_t np,
+                                                     const double *__restrict__ Lv, double dt,
+                                                     const int *__restrict__ blk_first, const int *__restrict__ blk_end,
+                                                     const int *__restrict__ blk_key, G g, const int *__restrict__ map,
+                                                     double *__restrict__ gout) {
+  __shared__ double acc[NB6 * 3];
+  for (int i = threadIdx.x; i < NB6 * 3; i += NT) acc[i] = 0.0;
+  __syncthreads();
+  const int key = blk_key[blockIdx.x];
+  const int o0 = (key % g.nb[0]) * 4, o1 = ((key / g.nb[0]) % g.nb[1]) * 4, o2 = (key / (g.nb[0] * g.nb[1])) * 4;
+  const int pe = blk_end[blockIdx.x];
+  for (int p = blk_first[blockIdx.x] + threadIdx.x; p < pe; p += NT) {
+    int b[3];
+    double fx[3], w[3][3], dw[3][3];
+    stencil(pd, np, p, g, b, fx, w, dw);
+    double F[9], P[9];
+    deformed(pd, np, p, Lv, nullptr, 0.0, dt, F);
+    const MatParams mp = mt[pmat[p]];
+    piola<double>(F, mp.mu, mp.lam, mp.model, P);
+    const double sc = dt * pd[PF_VOL * np + p];
+    double K[9];  // sc * P F^n^T
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        K[3 * a + c] = sc * (P[3 * a] * pd[(PF_F + 3 * c) * np + p] + P[3 * a + 1] * pd[(PF_F + 3 * c + 1) * np + p] +
+                             P[3 * a + 2] * pd[(PF_F + 3 * c + 2) * np + p]);
+    const int l0 = b[0] - o0, l1 = b[1] - o1, l2 = b[2] - o2;
+#pragma unroll
+    for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          double gw[3] = {dw[0][kx] * w[1][ky] * w[2][kz], w[0][kx] * dw[1][ky] * w[2][kz],
+                          w[0][kx] * w[1][ky] * dw[2][kz]};
+          double *a = acc + 3 * (((l2 + kz) * 6 + (l1 + ky)) * 6 + (l0 + kx));
+          atomicAdd(a, K[0] * gw[0] + K[1] * gw[1] + K[2] * gw[2]);
+          atomicAdd(a + 1, K[3] * gw[0] + K[4] * gw[1] + K[5] * gw[2]);
+          atomicAdd(a + 2, K[6] * gw[0] + K[7] * gw[1] + K[8] * gw[2]);
+        }
+  }
+  __syncthreads();
+  for (int li = threadIdx.x; li < NB6; li += NT) {
+    const double *a = acc + 3 * li;
+    if (a[0] == 0.0 && a[1] == 0.0 && a[2] == 0.0) continue;
+    int x = o0 + li % 6, y = o1 + (li / 6) % 6, z = o2 + li / 36;
+    if (x >= g.nd[0] || y >= g.nd[1] || z >= g.nd[2]) continue;
+    int idx = map[nlin(x, y, z, g.nd)];
+    if (idx < 0) continue;
+    atomicAdd(gout + 3 * idx, a[0]);
+    atomicAdd(gout + 3 * idx + 1, a[1]);
+    atomicAdd(gout + 3 * idx + 2, a[2]);
+  }
+}
+
+// node terms m_i (dv_i - dt g), projection, and the two termination norms
+__global__ void k_grad_nodes(int64_t nn, const double *__restrict__ m, const double *__restrict__ xi,
+                             const uint8_t *__restrict__ fixed, const double *__restrict__ dv, double dt, double g0,
+                             double g1, double g2, double cn_scale, double *__restrict__ gout,
+                             double *__restrict__ part) {
+  __shared__ double sh[NT];
+  double a2 = 0.0, c2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < nn; i += (int64_t)gridDim.x * NT) {
+    double r[3];
+    if (fixed[i]) {
+      r[0] = r[1] = r[2] = 0.0;
+    } else {
+      double mi = m[i];
+      r[0] = gout[3 * i] + mi * (dv[3 * i] - dt * g0);
+      r[1] = gout[3 * i + 1] + mi * (dv[3 * i + 1] - dt * g1);
+      r[2] = gout[3 * i + 2] + mi * (dv[3 * i + 2] - dt * g2);
+      double sq = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      a2 += sq;
+      double den = cn_scale * xi[i];
+      c2 += sq / (den * den);
+    }
+    gout[3 * i] = r[0];
+    gout[3 * i + 1] = r[1];
+    gout[3 * i + 2] = r[2];
+  }
+  double t = block_sum<NT>(a2, sh);
+  double u = block_sum<NT>(c2, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t;
+    part[2 * blockIdx.x + 1] = u;
+  }
+}
+
+template <class T>
+__global__ void k_stiffness(const double *__restrict__ pd, const int *__restrict__ pmat,
+                            const MatParams *__restrict__ mt, int64_t np, const double *__restrict__ Lv, double dt,
+                            T *__restrict__ A45) {
+  int64_t p = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  if (p >= np) return;
+  double Fd[9];
+  deformed(pd, np, p, Lv, nullptr, 0.0, dt, Fd);
+  T F[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) F[k] = (T)Fd[k];
+  const MatParams mp = mt[pmat[p]];
+  T A[45];
+  projected_stiffness<T>(F, (T)mp.mu, (T)mp.lam, mp.model, A);
+#pragma unroll
+  for (int k = 0; k < 45; ++k) A45[k * np + p] = A[k];
+}
+
+// ---------------------------------------------------------------------------
+// Fine Hessian: one CTA per occupied cell.  All particles of a cell share the
+// same 27 stencil nodes, so each of the 378 node pairs (i <= l) is summed over
+// the cell's particles in a register and added to the matrix once:
+//   H_il += dt^2 V_p sum_{g,d} A_p[(a,g),(b,d)] d_ig d_ld,  d_i = F^n^T grad w_ip
+// via B_i[a][b][d] = sum_g A_p[(a,g),(b,d)] d_ig (27 x 27 values per particle).
+// ---------------------------------------------------------------------------
+constexpr int HNT = 384;
+constexpr int NPAIR = 378;
+
+template <class T>
+__global__ void __launch_bounds__(HNT) k_hessian_cells(const double *__restrict__ pd, int64_t np,
+                                                      const T *__restrict__ A45, const int *__restrict__ cell_first,
+                                                      const int *__restrict__ cell_n, const int *__restrict__ cell_key,
+                                                      G g, double dt, const int *__restrict__ map,
+                                                      const int *__restrict__ row_ptr,
+                                                      const int *__restrict__ slotpos, T *__restrict__ vals) {
+  __shared__ T sA[81];
+  __shared__ T sd[27 * 3];
+  __shared__ T sB[27 * 27];
+  __shared__ int snode[27];
+  const int c = blockIdx.x;
+  const int first = cell_first[c], cnt = cell_n[c];
+  int cb[3];
+  {
+    unsigned key = (unsigned)cell_key[c];
+    unsigned B = key >> 6, l = key & 63u;
+    cb[0] = (int)(B % g.nb[0]) * 4 + (l & 3);
+    cb[1] = (int)((B / g.nb[0]) % g.nb[1]) * 4 + ((l >> 2) & 3);
+    cb[2] = (int)(B / (g.nb[0] * g.nb[1])) * 4 + (l >> 4);
+  }
+  if (threadIdx.x < 27) {
+    int k = threadIdx.x;
+    snode[k] = map[nlin(cb[0] + k % 3, cb[1] + (k / 3) % 3, cb[2] + k / 9, g.nd)];
+  }
+  // this thread's pair (i <= l) in stencil order
+  int pi = 0, pl = 0;
+  const bool has_pair = threadIdx.x < NPAIR;
+  if (has_pair) {
+    int t = threadIdx.x, i = 0;
+    while (t >= 27 - i) {
+      t -= 27 - i;
+      ++i;
+    }
+    pi = i;
+    pl = i + t;
+  }
+  T acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = T(0);
+  for (int q = 0; q < cnt; ++q) {
+    const int p = first + q;
+    __syncthreads();
+    if (threadIdx.x < 81) {
+      int r = threadIdx.x / 9, cc = threadIdx.x % 9;
+      double sc = dt * dt * pd[PF_VOL * np + p];
+      sA[threadIdx.x] = (T)(sc * (double)A45[sym45(r, cc) * np + p]);
+    } else if (threadIdx.x >= 96 && threadIdx.x < 96 + 27) {
+      int k = threadIdx.x - 96;
+      int kx = k % 3, ky = (k / 3) % 3, kz = k / 9;
+      double fx[3], w[3][3], dw[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        base_axis(pd[(PF_X + a) * np + p], g.o[a], g.inv_dx, &fx[a]);
+        bspline_axis<double>(fx[a], g.inv_dx, w[a], dw[a]);
+      }
+      double gw[3] = {dw[0][kx] * w[1][ky] * w[2][kz], w[0][kx] * dw[1][ky] * w[2][kz],
+                      w[0][kx] * w[1][ky] * dw[2][kz]};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)   // d_a = sum_b F_ba gw_b
+        sd[3 * k + a] = (T)(pd[(PF_F + a) * np + p] * gw[0] + pd[(PF_F + 3 + a) * np + p] * gw[1] +
+                            pd[(PF_F + 6 + a) * np + p] * gw[2]);
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < 27 * 27; o += HNT) {
+      int i = o / 27, abd = o % 27;
+      int a = abd / 9, b = (abd / 3) % 3, d = abd % 3;
+      sB[o] = sA[(3 * a) * 9 + 3 * b + d] * sd[3 * i] + sA[(3 * a + 1) * 9 + 3 * b + d] * sd[3 * i + 1] +
+              sA[(3 * a + 2) * 9 + 3 * b + d] * sd[3 * i + 2];
+    }
+    __syncthreads();
+    if (has_pair) {
+      const T *Bi = sB + 27 * pi;
+      const T dl0 = sd[3 * pl], dl1 = sd[3 * pl + 1], dl2 = sd[3 * pl + 2];
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) acc[ab] += Bi[3 * ab] * dl0 + Bi[3 * ab + 1] * dl1 + Bi[3 * ab + 2] * dl2;
+    }
+  }
+  __syncthreads();
+  if (!has_pair) return;
+  const int ri = snode[pi], rl = snode[pl];
+  const int s = (pl % 3 - pi % 3 + 2) + 5 * ((pl / 3) % 3 - (pi / 3) % 3 + 2) + 25 * (pl / 9 - pi / 9 + 2);
+  {
+    int rp = row_ptr[ri], nb = row_ptr[ri + 1] - rp;
+    int pos = slotpos[(int64_t)ri * NSLOT + s] - rp;
+    T *base = vals + 9 * (int64_t)rp + pos;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) atomicAdd(base + e * nb, acc[e]);
+  }
+  if (pi != pl) {
+    int rp = row_ptr[rl], nb = row_ptr[rl + 1] - rp;
+    int pos = slotpos[(int64_t)rl * NSLOT + (NSLOT - 1 - s)] - rp;
+    T *base = vals + 9 * (int64_t)rp + pos;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) atomicAdd(base + (3 * b + a) * nb, acc[3 * a + b]);
+  }
+}
+
+// mass term and Dirichlet projection: held rows/columns zeroed, held
+// diagonal m_i I (I when m_i = 0), free diagonal + m_i I.  One warp per row.
+template <class T>
+__global__ void k_hessian_finish(int64_t nn, const int *__restrict__ row_ptr, const int *__restrict__ cols,
+                                 const uint8_t *__restrict__ fixed, const double *__restrict__ m,
+                                 T *__restrict__ vals) {
+  int64_t i = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= nn) return;
+  int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
+  bool fi = fixed[i];
+  T *base = vals + 9 * (int64_t)rp;
+  for (int b = lane; b < nb; b += 32) {
+    int j = cols[rp + b];
+    if (fi || fixed[j]) {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) base[e * nb + b] = T(0);
+    }
+    if (j == i) {
+      double mi = m[i];
+      T d = fi ? (T)(mi > 0.0 ? mi : 1.0) : (T)mi;
+      base[0 * nb + b] += d;
+      base[4 * nb + b] += d;
+      base[8 * nb + b] += d;
+    }
+  }
+}
+}  // namespace
+
+void velocity_gradient(Scene &s, const double *u, const double *u2, double *L) {
+  if (s.np == 0) return;
+  k_velgrad<<<(unsigned)((s.np + NT - 1) / NT), NT, 0, s.st>>>(s.pd.p, s.np, geo(s), s.topo[0].map.p, u, u2, L);
+  HOT_LAUNCH("k_velgrad");
+}
+
+double energy(Scene &s, const double *L1, const double *L2, double alpha, const double *dvv, const double *pv) {
+  const int nbp = 2 * s.nsm, nbn = s.nsm;
+  s.part.ensure(4096);
+  if (alpha == 0.0) {
+    L2 = nullptr;
+    pv = nullptr;
+  }
+  k_energy<<<nbp + nbn, NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, L1, L2, alpha, s.dt, nbp, s.nn(), s.m.p,
+                                       dvv, pv, s.gravity[0], s.gravity[1], s.gravity[2], s.part.p);
+  HOT_LAUNCH("k_energy");
+  std::vector<double> h(nbp + nbn);
+  HOT_CUDA(cudaMemcpyAsync(h.data(), s.part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  double e = 0.0;
+  for (double x : h) e += x;
+  return e;
+}
+
+void gradient(Scene &s, const double *Lcur, const double *dvec, double *gout, double norms[2]) {
+  const int64_t nn = s.nn();
+  HOT_CUDA(cudaMemsetAsync(gout, 0, sizeof(double) * 3 * nn, s.st));
+  if (s.n_blocks > 0) {
+    k_grad_scatter<<<(unsigned)s.n_blocks, NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, Lcur, s.dt,
+                                                          s.blk_first.p, s.blk_end.p, s.blk_key.p, geo(s),
+                                                          s.topo[0].map.p, gout);
+    HOT_LAUNCH("k_grad_scatter");
+  }
+  const int nb = s.nsm;
+  s.part.ensure(4096);
+  double cn_scale = 24.0 * s.geo.dx * s.geo.dx * s.dt;
+  k_grad_nodes<<<nb, NT, 0, s.st>>>(nn, s.m.p, s.xi.p, s.fixed.p, dvec, s.dt, s.gravity[0], s.gravity[1],
+                                    s.gravity[2], cn_scale, gout, s.part.p);
+  HOT_LAUNCH("k_grad_nodes");
+  std::vector<double> h(2 * nb);
+  HOT_CUDA(cudaMemcpyAsync(h.data(), s.part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  norms[0] = norms[1] = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    norms[0] += h[2 * b];
+    norms[1] += h[2 * b + 1];
+  }
+}
+
+template <class T>
+void particle_stiffness(Scene &s, Hier<T> &h) {
+  h.A45.ensure((size_t)45 * s.np, 1.0);
+  if (s.np == 0) return;
+  k_stiffness<T><<<(unsigned)((s.np + 127) / 128), 128, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, s.Lv.p,
+                                                                  s.dt, h.A45.p);
+  HOT_LAUNCH("k_stiffness");
+}
+
+template <class T>
+void hessian_assemble(Scene &s, Hier<T> &h) {
+  Topo &t = s.topo[0];
+  Vals<T> &L = h.L[0];
+  L.vals.ensure(9 * (size_t)t.nnzb);
+  HOT_CUDA(cudaMemsetAsync(L.vals.p, 0, sizeof(T) * 9 * t.nnzb, s.st));
+  if (s.n_cells > 0) {
+    k_hessian_cells<T><<<(unsigned)s.n_cells, HNT, 0, s.st>>>(s.pd.p, s.np, h.A45.p, s.cell_first.p, s.cell_n.p,
+                                                             s.cell_key.p, geo(s), s.dt, t.map.p, t.row_ptr.p,
+                                                             t.slotpos.p, L.vals.p);
+    HOT_LAUNCH("k_hessian_cells");
+  }
+  if (t.n > 0) {
+    k_hessian_finish<T><<<(unsigned)((t.n + NT / 32 - 1) / (NT / 32)), NT, 0, s.st>>>(t.n, t.row_ptr.p, t.cols.p,
+                                                                                     s.fixed.p, s.m.p, L.vals.p);
+    HOT_LAUNCH("k_hessian_finish");
+  }
+}
+
+template void particle_stiffness<double>(Scene &, Hier<double> &);
+template void particle_stiffness<float>(Scene &, Hier<float> &);
+template void hessian_assemble<double>(Scene &, Hier<double> &);
+template void hessian_assemble<float>(Scene &, Hier<float> &);
+
+}  // namespace hot

@@ -1,0 +1,743 @@
+// Node-embedding Galerkin multigrid (Sec. 4) and the V-cycle of Alg. 2.
+//
+// Storage: each level keeps its 3x3 blocks in block-CSR with at most 125
+// blocks per row (offsets within +-2 per axis at every level, Sec. 6 "Sparse
+// matrix storage"); row i stores entry e (3a+b) of its k-th block at
+// vals[9*row_ptr[i] + e*nb_i + k], so that a warp reading one entry of 32
+// consecutive blocks touches 32 consecutive words.
+#include "internal.h"
+
+#include <cooperative_groups.h>
+
+namespace hot {
+
+namespace {
+constexpr int NT = 256;
+constexpr int WPB = NT / 32;
+
+__device__ __forceinline__ int64_t lin(int x, int y, int z, const int *nd) { return ((int64_t)z * nd[1] + y) * nd[0] + x; }
+
+struct Dims {
+  int d[3];
+};
+Dims dims_of(const Topo &t) {
+  Dims r;
+  for (int k = 0; k < 3; ++k) r.d[k] = t.dims[k];
+  return r;
+}
+
+// cell occupancy lookup (block-major keys of the particle sort)
+__device__ __forceinline__ bool cell_occupied(const int *cell_count, int x, int y, int z, const int *nb) {
+  unsigned B = ((unsigned)(z >> 2) * (unsigned)nb[1] + (unsigned)(y >> 2)) * (unsigned)nb[0] + (unsigned)(x >> 2);
+  unsigned key = B * 64u + (unsigned)(((z & 3) << 4) | ((y & 3) << 2) | (x & 3));
+  return cell_count[key] > 0;
+}
+
+// Level-0 pattern: block (i, l) exists iff some occupied cell has both nodes
+// in its 3^3 stencil, i.e. a cell c with max(i,l) - 2 <= c <= min(i,l) per axis.
+__global__ void k_pattern0(int64_t n, const int *__restrict__ coords, const int *__restrict__ map, Dims nd,
+                           const int *__restrict__ cell_count, int nb0, int nb1, int nb2, int cd0, int cd1, int cd2,
+                           uint32_t *__restrict__ mask, int *__restrict__ rowcnt) {
+  int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int nb[3] = {nb0, nb1, nb2};
+  const int cd[3] = {cd0, cd1, cd2};
+  int ci[3] = {coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]};
+  int count = 0;
+  for (int r = 0; r < 4; ++r) {
+    int s = r * 32 + lane;
+    bool present = false;
+    if (s < NSLOT) {
+      int o[3] = {s % 5 - 2, (s / 5) % 5 - 2, s / 25 - 2};
+      int cl[3];
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cl[k] = ci[k] + o[k];
+        ok = ok && cl[k] >= 0 && cl[k] < nd.d[k];
+      }
+      if (ok && map[lin(cl[0], cl[1], cl[2], nd.d)] >= 0) {
+        int lo[3], hi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          lo[k] = max(max(ci[k], cl[k]) - 2, 0);
+          hi[k] = min(min(ci[k], cl[k]), cd[k] - 1);
+        }
+        for (int z = lo[2]; z <= hi[2] && !present; ++z)
+          for (int y = lo[1]; y <= hi[1] && !present; ++y)
+            for (int x = lo[0]; x <= hi[0] && !present; ++x) present = cell_occupied(cell_count, x, y, z, nb);
+      }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, present);
+    if (lane == 0) mask[4 * i + r] = bal;
+    count += __popc(bal);
+  }
+  if (lane == 0) rowcnt[i] = count;
+}
+
+// cols / slotpos from the slot masks (columns in ascending slot order, which
+// is ascending node order for (z, y, x)-lexicographic numbering)
+__global__ void k_fill_pattern(int64_t n, const int *__restrict__ coords, const int *__restrict__ map, Dims nd,
+                               const uint32_t *__restrict__ mask, const int *__restrict__ row_ptr,
+                               int *__restrict__ cols, int *__restrict__ slotpos) {
+  int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  int ci[3] = {coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]};
+  int base = row_ptr[i];
+  int before = 0;
+  for (int r = 0; r < 4; ++r) {
+    uint32_t mk = mask[4 * i + r];
+    int s = r * 32 + lane;
+    bool on = (mk >> lane) & 1u;
+    int rank = before + __popc(mk & ((1u << lane) - 1u));
+    if (s < NSLOT) {
+      if (on) {
+        int o[3] = {s % 5 - 2, (s / 5) % 5 - 2, s / 25 - 2};
+        cols[base + rank] = map[lin(ci[0] + o[0], ci[1] + o[1], ci[2] + o[2], nd.d)];
+        slotpos[i * NSLOT + s] = base + rank;
+      } else {
+        slotpos[i * NSLOT + s] = -1;
+      }
+    }
+    before += __popc(mk);
+  }
+}
+
+// coarse node candidates of every fine node: |a - 2A| <= 1 per axis
+__global__ void k_mark_coarse(int64_t n, const int *__restrict__ coords, Dims cd, uint8_t *__restrict__ flag) {
+  int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (i >= n) return;
+  int a[3] = {coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]};
+  int lo[3], cnt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = (a[k] & 1) ? (a[k] - 1) >> 1 : a[k] >> 1;
+    cnt[k] = (a[k] & 1) ? 2 : 1;
+  }
+  for (int z = 0; z < cnt[2]; ++z)
+    for (int y = 0; y < cnt[1]; ++y)
+      for (int x = 0; x < cnt[0]; ++x) flag[lin(lo[0] + x, lo[1] + y, lo[2] + z, cd.d)] = 1;
+}
+
+// symbolic Galerkin product: coarse (J, K) exists iff some fine a embedded in J
+// has a block (a, c) with c embedded in K.  One warp per coarse row.
+__global__ void k_pattern_rap(int64_t nc, const int *__restrict__ ccoords, const int *__restrict__ fmap, Dims fd,
+                              const int *__restrict__ fcoords, const int *__restrict__ frow_ptr,
+                              const int *__restrict__ fcols, uint32_t *__restrict__ mask, int *__restrict__ rowcnt) {
+  __shared__ uint32_t smask[WPB][4];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t J = (int64_t)blockIdx.x * WPB + w;
+  if (lane < 4) smask[w][lane] = 0u;
+  __syncwarp();
+  if (J < nc) {
+    int cj[3] = {ccoords[3 * J], ccoords[3 * J + 1], ccoords[3 * J + 2]};
+    for (int o = 0; o < 27; ++o) {
+      int a[3] = {2 * cj[0] + o % 3 - 1, 2 * cj[1] + (o / 3) % 3 - 1, 2 * cj[2] + o / 9 - 1};
+      if (a[0] < 0 || a[1] < 0 || a[2] < 0 || a[0] >= fd.d[0] || a[1] >= fd.d[1] || a[2] >= fd.d[2]) continue;
+      int ia = fmap[lin(a[0], a[1], a[2], fd.d)];
+      if (ia < 0) continue;
+      for (int b = frow_ptr[ia] + lane; b < frow_ptr[ia + 1]; b += 32) {
+        int c = fcols[b];
+        int cc[3] = {fcoords[3 * c], fcoords[3 * c + 1], fcoords[3 * c + 2]};
+        int lo[3], cnt[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          lo[k] = (cc[k] & 1) ? (cc[k] - 1) >> 1 : cc[k] >> 1;
+          cnt[k] = (cc[k] & 1) ? 2 : 1;
+        }
+        for (int z = 0; z < cnt[2]; ++z)
+          for (int y = 0; y < cnt[1]; ++y)
+            for (int x = 0; x < cnt[0]; ++x) {
+              int s = (lo[0] + x - cj[0] + 2) + 5 * (lo[1] + y - cj[1] + 2) + 25 * (lo[2] + z - cj[2] + 2);
+              atomicOr(&smask[w][s >> 5], 1u << (s & 31));
+            }
+      }
+    }
+  }
+  __syncwarp();
+  if (J < nc && lane < 4) {
+    uint32_t mk = smask[w][lane];
+    mask[4 * J + lane] = mk;
+    int c = __popc(mk);
+    c += __shfl_down_sync(0xfu, c, 2, 4);
+    c += __shfl_down_sync(0xfu, c, 1, 4);
+    if (lane == 0) rowcnt[J] = c;
+  }
+}
+
+__device__ __forceinline__ float embed_w(int d) { return d == 0 ? 1.0f : 0.5f; }
+
+// numeric Galerkin product H^{m+1} = R H^m R^T, one CTA per coarse row J,
+// its 125 slots accumulated in shared memory
+template <class T>
+__global__ void __launch_bounds__(128) k_rap(int64_t nc, const int *__restrict__ ccoords, const int *__restrict__ crow_ptr,
+                                             const int *__restrict__ cslotpos, T *__restrict__ cvals,
+                                             const int *__restrict__ fmap, Dims fd, const int *__restrict__ fcoords,
+                                             const int *__restrict__ frow_ptr, const int *__restrict__ fcols,
+                                             const T *__restrict__ fvals) {
+  __shared__ T acc[NSLOT * 9];
+  const int64_t J = blockIdx.x;
+  for (int k = threadIdx.x; k < NSLOT * 9; k += 128) acc[k] = T(0);
+  __syncthreads();
+  int cj[3] = {ccoords[3 * J], ccoords[3 * J + 1], ccoords[3 * J + 2]};
+  for (int o = 0; o < 27; ++o) {
+    int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+    int a[3] = {2 * cj[0] + ox, 2 * cj[1] + oy, 2 * cj[2] + oz};
+    if (a[0] < 0 || a[1] < 0 || a[2] < 0 || a[0] >= fd.d[0] || a[1] >= fd.d[1] || a[2] >= fd.d[2]) continue;
+    int ia = fmap[lin(a[0], a[1], a[2], fd.d)];
+    if (ia < 0) continue;
+    const T rJa = (T)(embed_w(ox) * embed_w(oy) * embed_w(oz));
+    const int rp = frow_ptr[ia], nb = frow_ptr[ia + 1] - rp;
+    const T *fv = fvals + 9 * (int64_t)rp;
+    for (int b = threadIdx.x; b < nb; b += 128) {
+      int c = fcols[rp + b];
+      int cc[3] = {fcoords[3 * c], fcoords[3 * c + 1], fcoords[3 * c + 2]};
+      T h[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) h[e] = rJa * fv[e * nb + b];
+      int lo[3], cnt[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = (cc[k] & 1) ? (cc[k] - 1) >> 1 : cc[k] >> 1;
+        cnt[k] = (cc[k] & 1) ? 2 : 1;
+      }
+      for (int z = 0; z < cnt[2]; ++z)
+        for (int y = 0; y < cnt[1]; ++y)
+          for (int x = 0; x < cnt[0]; ++x) {
+            int K[3] = {lo[0] + x, lo[1] + y, lo[2] + z};
+            T rKc = (T)(embed_w(cc[0] - 2 * K[0]) * embed_w(cc[1] - 2 * K[1]) * embed_w(cc[2] - 2 * K[2]));
+            int s = (K[0] - cj[0] + 2) + 5 * (K[1] - cj[1] + 2) + 25 * (K[2] - cj[2] + 2);
+            T *dst = acc + 9 * s;
+#pragma unroll
+            for (int e = 0; e < 9; ++e) atomicAdd(dst + e, rKc * h[e]);
+          }
+    }
+  }
+  __syncthreads();
+  const int rp = crow_ptr[J], nb = crow_ptr[J + 1] - rp;
+  T *cv = cvals + 9 * (int64_t)rp;
+  for (int k = threadIdx.x; k < NSLOT * 9; k += 128) {
+    int s = k / 9, e = k % 9;
+    int pos = cslotpos[J * NSLOT + s];
+    if (pos >= 0) cv[e * nb + (pos - rp)] = acc[k];
+  }
+}
+
+// inverse of each diagonal block and the scalar diagonal
+template <class T>
+__global__ void k_diag(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ slotpos,
+                       const T *__restrict__ vals, T *__restrict__ dinv, T *__restrict__ diag) {
+  int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (i >= n) return;
+  int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
+  int pos = slotpos[i * NSLOT + DIAG_SLOT] - rp;
+  T D[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) D[e] = vals[9 * (int64_t)rp + e * nb + pos];
+  T c[9];
+  cofactor3(D, c);
+  T det = D[0] * c[0] + D[1] * c[1] + D[2] * c[2];
+  T inv = T(1) / det;
+  // inverse = cof^T / det
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) dinv[9 * i + 3 * a + b] = c[3 * b + a] * inv;
+  diag[3 * i] = D[0];
+  diag[3 * i + 1] = D[4];
+  diag[3 * i + 2] = D[8];
+}
+
+// 27-coloring c = (x mod 3) + 3 (y mod 3) + 9 (z mod 3)
+__global__ void k_color_count(int64_t n, const int *__restrict__ coords, int *__restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (i >= n) return;
+  int c = coords[3 * i] % 3 + 3 * (coords[3 * i + 1] % 3) + 9 * (coords[3 * i + 2] % 3);
+  atomicAdd(&cnt[c], 1);
+}
+__global__ void k_color_fill(int64_t n, const int *__restrict__ coords, int *__restrict__ cursor,
+                             int *__restrict__ list) {
+  int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (i >= n) return;
+  int c = coords[3 * i] % 3 + 3 * (coords[3 * i + 1] % 3) + 9 * (coords[3 * i + 2] % 3);
+  list[atomicAdd(&cursor[c], 1)] = (int)i;
+}
+
+// ---------------------------------------------------------------------------
+// smoothing and transfer kernels (one warp per row)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void row_product(int64_t i, int lane, const int *__restrict__ row_ptr,
+                                            const int *__restrict__ cols, const T *__restrict__ vals,
+                                            const T *u, bool skip_diag, T acc[3]) {
+  const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
+  const T *v = vals + 9 * (int64_t)rp;
+  acc[0] = acc[1] = acc[2] = T(0);
+  for (int b = lane; b < nb; b += 32) {
+    int j = cols[rp + b];
+    if (skip_diag && j == i) continue;
+    T u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
+    acc[0] += v[b] * u0 + v[nb + b] * u1 + v[2 * nb + b] * u2;
+    acc[1] += v[3 * nb + b] * u0 + v[4 * nb + b] * u1 + v[5 * nb + b] * u2;
+    acc[2] += v[6 * nb + b] * u0 + v[7 * nb + b] * u1 + v[8 * nb + b] * u2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+    acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
+    acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
+  }
+}
+
+// one color of a Gauss-Seidel sweep: u_i <- D_i^{-1} (b_i - sum_{j != i} H_ij u_j)
+template <class T>
+__global__ void k_sgs_color(const int *__restrict__ list, int nrows, const int *__restrict__ row_ptr,
+                            const int *__restrict__ cols, const T *__restrict__ vals, const T *__restrict__ dinv,
+                            const T *__restrict__ b, T *u) {
+  int w = blockIdx.x * WPB + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  int64_t i = list[w];
+  T acc[3];
+  row_product<T>(i, lane, row_ptr, cols, vals, u, true, acc);
+  if (lane == 0) {
+    T y0 = b[3 * i] - acc[0], y1 = b[3 * i + 1] - acc[1], y2 = b[3 * i + 2] - acc[2];
+    const T *D = dinv + 9 * i;
+    u[3 * i] = D[0] * y0 + D[1] * y1 + D[2] * y2;
+    u[3 * i + 1] = D[3] * y0 + D[4] * y1 + D[5] * y2;
+    u[3 * i + 2] = D[6] * y0 + D[7] * y1 + D[8] * y2;
+  }
+}
+
+// r = b - H u
+template <class T>
+__global__ void k_residual(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ cols,
+                           const T *__restrict__ vals, const T *__restrict__ b, const T *__restrict__ u,
+                           T *__restrict__ r) {
+  int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  T acc[3];
+  row_product<T>(i, lane, row_ptr, cols, vals, u, false, acc);
+  if (lane == 0) {
+    r[3 * i] = b[3 * i] - acc[0];
+    r[3 * i + 1] = b[3 * i + 1] - acc[1];
+    r[3 * i + 2] = b[3 * i + 2] - acc[2];
+  }
+}
+
+// b^{m+1}_J = sum_a R_Ja r_a over the 27 fine nodes a = 2J + o
+template <class T>
+__global__ void k_restrict(int64_t nc, const int *__restrict__ ccoords, const int *__restrict__ fmap, Dims fd,
+                           const T *__restrict__ r, T *__restrict__ bc) {
+  int64_t J = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (J >= nc) return;
+  int cj[3] = {ccoords[3 * J], ccoords[3 * J + 1], ccoords[3 * J + 2]};
+  T acc[3] = {T(0), T(0), T(0)};
+  for (int o = 0; o < 27; ++o) {
+    int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+    int a[3] = {2 * cj[0] + ox, 2 * cj[1] + oy, 2 * cj[2] + oz};
+    if (a[0] < 0 || a[1] < 0 || a[2] < 0 || a[0] >= fd.d[0] || a[1] >= fd.d[1] || a[2] >= fd.d[2]) continue;
+    int ia = fmap[lin(a[0], a[1], a[2], fd.d)];
+    if (ia < 0) continue;
+    T w = (T)(embed_w(ox) * embed_w(oy) * embed_w(oz));
+    acc[0] += w * r[3 * ia];
+    acc[1] += w * r[3 * ia + 1];
+    acc[2] += w * r[3 * ia + 2];
+  }
+  bc[3 * J] = acc[0];
+  bc[3 * J + 1] = acc[1];
+  bc[3 * J + 2] = acc[2];
+}
+
+// u^m_a += sum_J R_Ja u^{m+1}_J over the 1..8 coarse parents of a
+template <class T>
+__global__ void k_prolong_add(int64_t nf, const int *__restrict__ fcoords, const int *__restrict__ cmap, Dims cd,
+                              const T *__restrict__ uc, T *__restrict__ uf) {
+  int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (i >= nf) return;
+  int a[3] = {fcoords[3 * i], fcoords[3 * i + 1], fcoords[3 * i + 2]};
+  int lo[3], cnt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = (a[k] & 1) ? (a[k] - 1) >> 1 : a[k] >> 1;
+    cnt[k] = (a[k] & 1) ? 2 : 1;
+  }
+  T w = (T)(embed_w(cnt[0] - 1) * embed_w(cnt[1] - 1) * embed_w(cnt[2] - 1));
+  T acc[3] = {T(0), T(0), T(0)};
+  for (int z = 0; z < cnt[2]; ++z)
+    for (int y = 0; y < cnt[1]; ++y)
+      for (int x = 0; x < cnt[0]; ++x) {
+        int J = cmap[lin(lo[0] + x, lo[1] + y, lo[2] + z, cd.d)];
+        acc[0] += uc[3 * J];
+        acc[1] += uc[3 * J + 1];
+        acc[2] += uc[3 * J + 2];
+      }
+  uf[3 * i] += w * acc[0];
+  uf[3 * i + 1] += w * acc[1];
+  uf[3 * i + 2] += w * acc[2];
+}
+
+template <class T>
+__global__ void k_load_rhs(int64_t n, const double *__restrict__ src, const uint8_t *__restrict__ fixed,
+                           T *__restrict__ dst) {
+  int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (k >= 3 * n) return;
+  dst[k] = fixed[k / 3] ? T(0) : (T)src[k];
+}
+template <class T>
+__global__ void k_store_out(int64_t n, const T *__restrict__ src, const uint8_t *__restrict__ fixed,
+                            double *__restrict__ dst) {
+  int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (k >= 3 * n) return;
+  dst[k] = fixed[k / 3] ? 0.0 : (double)src[k];
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: Jacobi-preconditioned CG in one cooperative launch.  The
+// stopping rule is the adaptive one of Sec. 5.3 read as
+//   k = min(1/2, sqrt(max(sqrt(b^T D^-1 b), tau))),  stop when
+//   sqrt(r^T D^-1 r) <= k sqrt(b^T D^-1 b),
+// with D the scalar diagonal.  Every block sums the same partials in the same
+// order, so all blocks take the same branch.  The grid barrier gives up after
+// a bounded number of polls and reports DEV_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr long long BARRIER_SPIN_LIMIT = 1ll << 24;
+
+__device__ bool grid_sync(unsigned *bar, unsigned &gen, int *err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    unsigned arrived = atomicAdd(&bar[0], 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      long long spins = 0;
+      while (*((volatile unsigned *)&bar[1]) == gen) {
+        if (!keep_waiting(spins, BARRIER_SPIN_LIMIT)) {
+          ok = 0;
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  gen += 1;
+  __syncthreads();
+  return ok != 0;
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ cols,
+                                                   const T *__restrict__ vals, const T *__restrict__ diag,
+                                                   const T *__restrict__ b, T *x, T *r, T *z, T *p, T *Ap,
+                                                   double *part, unsigned *bar, int *info, int *err, double tau,
+                                                   int max_iter, int forced) {
+  __shared__ double sh[NT];
+  unsigned gen = 0;
+  const int64_t n3 = 3 * n;
+  const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x, gstride = (int64_t)gridDim.x * NT;
+  const int G = gridDim.x;
+  double *partA = part, *partB = part + G;
+  // x = 0, r = b, z = D^-1 r, p = z, partial r^T z
+  double acc = 0.0;
+  for (int64_t k = gtid; k < n3; k += gstride) {
+    T bk = b[k];
+    x[k] = T(0);
+    r[k] = bk;
+    T zk = bk / diag[k];
+    z[k] = zk;
+    p[k] = zk;
+    acc += (double)bk * (double)zk;
+  }
+  double t = block_sum<NT>(acc, sh);
+  if (threadIdx.x == 0) partA[blockIdx.x] = t;
+  if (!grid_sync(bar, gen, err)) return;
+  double rz = sum_partials<NT>(partA, G, sh);
+  const double bn = sqrt(fmax(rz, 0.0));
+  const double kk = fmin(0.5, sqrt(fmax(bn, tau)));
+  int it = 0;
+  while (true) {
+    if (forced >= 0) {
+      if (it >= forced) break;
+    } else if (sqrt(fmax(rz, 0.0)) <= kk * bn || it >= max_iter) {
+      break;
+    }
+    // Ap = H p, partial p^T Ap
+    acc = 0.0;
+    const int warps = G * (NT / 32);
+    for (int64_t i = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); i < n; i += warps) {
+      T a3[3];
+      row_product<T>(i, threadIdx.x & 31, row_ptr, cols, vals, p, false, a3);
+      if ((threadIdx.x & 31) == 0) {
+        Ap[3 * i] = a3[0];
+        Ap[3 * i + 1] = a3[1];
+        Ap[3 * i + 2] = a3[2];
+        acc += (double)p[3 * i] * (double)a3[0] + (double)p[3 * i + 1] * (double)a3[1] +
+               (double)p[3 * i + 2] * (double)a3[2];
+      }
+    }
+    t = block_sum<NT>(acc, sh);
+    if (threadIdx.x == 0) partB[blockIdx.x] = t;
+    if (!grid_sync(bar, gen, err)) return;
+    double pAp = sum_partials<NT>(partB, G, sh);
+    if (!(pAp > 0.0)) break;
+    const double alpha = rz / pAp;
+    acc = 0.0;
+    for (int64_t k = gtid; k < n3; k += gstride) {
+      T xk = x[k] + (T)alpha * p[k];
+      T rk = r[k] - (T)alpha * Ap[k];
+      x[k] = xk;
+      r[k] = rk;
+      T zk = rk / diag[k];
+      z[k] = zk;
+      acc += (double)rk * (double)zk;
+    }
+    t = block_sum<NT>(acc, sh);
+    if (threadIdx.x == 0) partA[blockIdx.x] = t;
+    if (!grid_sync(bar, gen, err)) return;
+    double rz_new = sum_partials<NT>(partA, G, sh);
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (int64_t k = gtid; k < n3; k += gstride) p[k] = z[k] + (T)beta * p[k];
+    ++it;
+    if (!grid_sync(bar, gen, err)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = it;
+}
+
+template <class T>
+int coop_blocks() {
+  static int cached = -1;
+  if (cached < 0) {
+    int per_sm = 0;
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_pcg<T>, NT, 0));
+    int dev = 0, nsm = 0;
+    HOT_CUDA(cudaGetDevice(&dev));
+    HOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    cached = per_sm * nsm;
+    if (cached < 1) cached = 1;
+  }
+  return cached;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+void build_pattern0(Scene &s) {
+  Topo &t = s.topo[0];
+  const int64_t n = t.n;
+  t.mask.ensure(4 * (size_t)n + 4);
+  t.rowcnt.ensure(n + 1);
+  t.row_ptr.ensure(n + 1);
+  t.slotpos.ensure((size_t)NSLOT * n + NSLOT);
+  if (n == 0) {
+    t.nnzb = 0;
+    HOT_CUDA(cudaMemsetAsync(t.row_ptr.p, 0, sizeof(int), s.st));
+    return;
+  }
+  unsigned nbw = (unsigned)((n + WPB - 1) / WPB);
+  k_pattern0<<<nbw, NT, 0, s.st>>>(n, t.coords.p, t.map.p, dims_of(t), s.cell_count.p, s.geo.nb[0], s.geo.nb[1],
+                                   s.geo.nb[2], s.geo.dims[0], s.geo.dims[1], s.geo.dims[2], t.mask.p, t.rowcnt.p);
+  HOT_LAUNCH("k_pattern0");
+  HOT_CUDA(cudaMemsetAsync(t.rowcnt.p + n, 0, sizeof(int), s.st));
+  exclusive_scan(t.rowcnt.p, t.row_ptr.p, n + 1, s.scan, s.st);
+  t.nnzb = read_scan_total(s.scan, s.st);
+  t.cols.ensure(t.nnzb);
+  k_fill_pattern<<<nbw, NT, 0, s.st>>>(n, t.coords.p, t.map.p, dims_of(t), t.mask.p, t.row_ptr.p, t.cols.p,
+                                       t.slotpos.p);
+  HOT_LAUNCH("k_fill_pattern");
+}
+
+void build_coarse_topology(Scene &s, int m) {
+  Topo &F = s.topo[m];
+  Topo &C = s.topo[m + 1];
+  for (int k = 0; k < 3; ++k) C.dims[k] = F.dims[k] / 2 + 1;
+  int64_t ntot = (int64_t)C.dims[0] * C.dims[1] * C.dims[2];
+  C.flag.ensure(ntot, 1.0);
+  C.map.ensure(ntot, 1.0);
+  HOT_CUDA(cudaMemsetAsync(C.flag.p, 0, ntot, s.st));
+  if (F.n > 0) {
+    k_mark_coarse<<<(unsigned)((F.n + NT - 1) / NT), NT, 0, s.st>>>(F.n, F.coords.p, dims_of(C), C.flag.p);
+    HOT_LAUNCH("k_mark_coarse");
+  }
+  compact_dense(s, C);
+  const int64_t n = C.n;
+  C.mask.ensure(4 * (size_t)n + 4);
+  C.rowcnt.ensure(n + 1);
+  C.row_ptr.ensure(n + 1);
+  C.slotpos.ensure((size_t)NSLOT * n + NSLOT);
+  if (n == 0) {
+    C.nnzb = 0;
+    return;
+  }
+  unsigned nbw = (unsigned)((n + WPB - 1) / WPB);
+  k_pattern_rap<<<nbw, NT, 0, s.st>>>(n, C.coords.p, F.map.p, dims_of(F), F.coords.p, F.row_ptr.p, F.cols.p, C.mask.p,
+                                      C.rowcnt.p);
+  HOT_LAUNCH("k_pattern_rap");
+  HOT_CUDA(cudaMemsetAsync(C.rowcnt.p + n, 0, sizeof(int), s.st));
+  exclusive_scan(C.rowcnt.p, C.row_ptr.p, n + 1, s.scan, s.st);
+  C.nnzb = read_scan_total(s.scan, s.st);
+  C.cols.ensure(C.nnzb);
+  k_fill_pattern<<<nbw, NT, 0, s.st>>>(n, C.coords.p, C.map.p, dims_of(C), C.mask.p, C.row_ptr.p, C.cols.p,
+                                       C.slotpos.p);
+  HOT_LAUNCH("k_fill_pattern");
+}
+
+void build_colors(Scene &s, int m) {
+  Topo &t = s.topo[m];
+  t.color_cnt.ensure(28);
+  t.color_list.ensure(t.n + 1);
+  HOT_CUDA(cudaMemsetAsync(t.color_cnt.p, 0, sizeof(int) * 28, s.st));
+  if (t.n == 0) {
+    for (int c = 0; c < 28; ++c) t.color_off[c] = 0;
+    return;
+  }
+  unsigned nb = (unsigned)((t.n + NT - 1) / NT);
+  k_color_count<<<nb, NT, 0, s.st>>>(t.n, t.coords.p, t.color_cnt.p);
+  HOT_LAUNCH("k_color_count");
+  int cnt[28];
+  HOT_CUDA(cudaMemcpyAsync(cnt, t.color_cnt.p, sizeof(int) * 27, cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  t.color_off[0] = 0;
+  for (int c = 0; c < 27; ++c) t.color_off[c + 1] = t.color_off[c] + cnt[c];
+  HOT_CUDA(cudaMemcpyAsync(t.color_cnt.p, t.color_off, sizeof(int) * 27, cudaMemcpyHostToDevice, s.st));
+  k_color_fill<<<nb, NT, 0, s.st>>>(t.n, t.coords.p, t.color_cnt.p, t.color_list.p);
+  HOT_LAUNCH("k_color_fill");
+  HOT_CUDA(cudaStreamSynchronize(s.st));   // color_off (host) must outlive the async copy
+}
+
+template <class T>
+void rap(Scene &s, Hier<T> &h, int m) {
+  Topo &F = s.topo[m];
+  Topo &C = s.topo[m + 1];
+  Vals<T> &VC = h.L[m + 1];
+  VC.vals.ensure(9 * (size_t)C.nnzb + 9);
+  if (C.n == 0) return;
+  k_rap<T><<<(unsigned)C.n, 128, 0, s.st>>>(C.n, C.coords.p, C.row_ptr.p, C.slotpos.p, VC.vals.p, F.map.p, dims_of(F),
+                                            F.coords.p, F.row_ptr.p, F.cols.p, h.L[m].vals.p);
+  HOT_LAUNCH("k_rap");
+}
+
+template <class T>
+void finalize_values(Scene &s, Hier<T> &h, int m) {
+  Topo &t = s.topo[m];
+  Vals<T> &V = h.L[m];
+  V.dinv.ensure(9 * (size_t)t.n + 9);
+  V.diag.ensure(3 * (size_t)t.n + 3);
+  V.u.ensure(3 * (size_t)t.n + 3);
+  V.b.ensure(3 * (size_t)t.n + 3);
+  V.r.ensure(3 * (size_t)t.n + 3);
+  if (t.n == 0) return;
+  k_diag<T><<<(unsigned)((t.n + NT - 1) / NT), NT, 0, s.st>>>(t.n, t.row_ptr.p, t.slotpos.p, V.vals.p, V.dinv.p,
+                                                              V.diag.p);
+  HOT_LAUNCH("k_diag");
+}
+
+namespace {
+template <class T>
+void sgs_sweep(Scene &s, Topo &t, Vals<T> &V, bool forward) {
+  for (int k = 0; k < 27; ++k) {
+    int c = forward ? k : 26 - k;
+    int nr = t.color_off[c + 1] - t.color_off[c];
+    if (nr == 0) continue;
+    k_sgs_color<T><<<(unsigned)((nr + WPB - 1) / WPB), NT, 0, s.st>>>(t.color_list.p + t.color_off[c], nr,
+                                                                       t.row_ptr.p, t.cols.p, V.vals.p, V.dinv.p,
+                                                                       V.b.p, V.u.p);
+    HOT_LAUNCH("k_sgs_color");
+  }
+}
+
+template <class T>
+int coarse_solve(Scene &s, Hier<T> &h, int m, int forced) {
+  Topo &t = s.topo[m];
+  Vals<T> &V = h.L[m];
+  const int64_t n = t.n;
+  h.x.ensure(3 * n + 3);
+  h.r.ensure(3 * n + 3);
+  h.z.ensure(3 * n + 3);
+  h.p.ensure(3 * n + 3);
+  h.Ap.ensure(3 * n + 3);
+  h.bar.ensure(2);
+  h.info.ensure(2);
+  int G = (int)((n + WPB * 2 - 1) / (WPB * 2));
+  int maxb = coop_blocks<T>();
+  if (G > maxb) G = maxb;
+  if (G < 1) G = 1;
+  h.part.ensure(2 * (size_t)G);
+  HOT_CUDA(cudaMemsetAsync(h.bar.p, 0, 2 * sizeof(unsigned), s.st));
+  HOT_CUDA(cudaMemsetAsync(h.info.p, 0, 2 * sizeof(int), s.st));
+  int max_iter = s.opts.max_coarse_cg > 0 ? s.opts.max_coarse_cg : (int)(3 * n);
+  double tau = s.opts.eps;
+  int64_t nn = n;
+  const int *rp = t.row_ptr.p;
+  const int *cl = t.cols.p;
+  const T *vv = V.vals.p;
+  const T *dg = V.diag.p;
+  const T *bb = V.b.p;
+  T *xx = h.x.p, *rr = h.r.p, *zz = h.z.p, *pp = h.p.p, *ap = h.Ap.p;
+  double *pt = h.part.p;
+  unsigned *br = h.bar.p;
+  int *inf = h.info.p;
+  int *er = s.errflag.p;
+  void *args[] = {&nn, &rp, &cl, &vv, &dg, &bb, &xx, &rr, &zz, &pp, &ap, &pt, &br, &inf, &er, &tau, &max_iter, &forced};
+  HOT_CUDA(cudaLaunchCooperativeKernel((void *)k_coarse_pcg<T>, dim3(G), dim3(NT), args, 0, s.st));
+  int its = 0;
+  HOT_CUDA(cudaMemcpyAsync(&its, h.info.p, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaMemcpyAsync(V.u.p, h.x.p, sizeof(T) * 3 * n, cudaMemcpyDeviceToDevice, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  return its;
+}
+}  // namespace
+
+// Alg. 2: returns the coarsest PCG iteration count
+template <class T>
+int vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, int forced_cg) {
+  const int M = s.nlev;
+  Topo &t0 = s.topo[0];
+  if (t0.n == 0) return 0;
+  k_load_rhs<T><<<(unsigned)((3 * t0.n + NT - 1) / NT), NT, 0, s.st>>>(t0.n, b_in, s.fixed.p, h.L[0].b.p);
+  HOT_LAUNCH("k_load_rhs");
+  for (int m = 0; m < M - 1; ++m) {
+    Topo &t = s.topo[m];
+    Vals<T> &V = h.L[m];
+    HOT_CUDA(cudaMemsetAsync(V.u.p, 0, sizeof(T) * 3 * t.n, s.st));
+    sgs_sweep<T>(s, t, V, true);
+    sgs_sweep<T>(s, t, V, false);
+    k_residual<T><<<(unsigned)((t.n + WPB - 1) / WPB), NT, 0, s.st>>>(t.n, t.row_ptr.p, t.cols.p, V.vals.p, V.b.p,
+                                                                       V.u.p, V.r.p);
+    HOT_LAUNCH("k_residual");
+    Topo &c = s.topo[m + 1];
+    k_restrict<T><<<(unsigned)((c.n + NT - 1) / NT), NT, 0, s.st>>>(c.n, c.coords.p, t.map.p, dims_of(t), V.r.p,
+                                                                     h.L[m + 1].b.p);
+    HOT_LAUNCH("k_restrict");
+  }
+  int its = coarse_solve<T>(s, h, M - 1, forced_cg);
+  for (int m = M - 2; m >= 0; --m) {
+    Topo &t = s.topo[m];
+    Topo &c = s.topo[m + 1];
+    Vals<T> &V = h.L[m];
+    k_prolong_add<T><<<(unsigned)((t.n + NT - 1) / NT), NT, 0, s.st>>>(t.n, t.coords.p, c.map.p, dims_of(c),
+                                                                       h.L[m + 1].u.p, V.u.p);
+    HOT_LAUNCH("k_prolong_add");
+    sgs_sweep<T>(s, t, V, true);
+    sgs_sweep<T>(s, t, V, false);
+  }
+  k_store_out<T><<<(unsigned)((3 * t0.n + NT - 1) / NT), NT, 0, s.st>>>(t0.n, h.L[0].u.p, s.fixed.p, u_out);
+  HOT_LAUNCH("k_store_out");
+  return its;
+}
+
+template void rap<double>(Scene &, Hier<double> &, int);
+template void rap<float>(Scene &, Hier<float> &, int);
+template void finalize_values<double>(Scene &, Hier<double> &, int);
+template void finalize_values<float>(Scene &, Hier<float> &, int);
+template int vcycle<double>(Scene &, Hier<double> &, const double *, double *, int);
+template int vcycle<float>(Scene &, Hier<float> &, const double *, double *, int);
+
+}  // namespace hot

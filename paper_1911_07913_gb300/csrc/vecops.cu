@@ -1,0 +1,189 @@
+// Node-vector operations in float64 for the L-BFGS loop of Alg. 3.  Every
+// reduction uses a fixed grid and sums its partials in a fixed order, so
+// results are bitwise reproducible run to run.
+#include "internal.h"
+
+namespace hot {
+
+namespace {
+constexpr int NT = 256;
+
+__global__ void k_dot3(const double *__restrict__ x, const double *__restrict__ y, int64_t n, int mode,
+                       double *__restrict__ part) {
+  __shared__ double sh[NT];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT) {
+    double xv = x[k], yv = y[k];
+    a += xv * yv;
+    if (mode) {
+      b += xv * xv;
+      c += yv * yv;
+    }
+  }
+  a = block_sum<NT>(a, sh);
+  if (mode) {
+    b = block_sum<NT>(b, sh);
+    c = block_sum<NT>(c, sh);
+  }
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
+  }
+}
+
+__global__ void k_axpy(double *__restrict__ y, double a, const double *__restrict__ x, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT) y[k] += a * x[k];
+}
+__global__ void k_lincomb(double *z, double a, const double *x, double b, const double *y, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT)
+    z[k] = a * x[k] + (y ? b * y[k] : 0.0);
+}
+
+// Two-loop steps with the scalar coefficient formed on the device from the
+// previous step's partials:
+//   first loop : alpha_a = rho_a s_a^T q;  q <- q - alpha_a y_a
+//   second loop: beta = rho_a y_a^T r;     r <- r + (alpha_a - beta) s_a
+// Each launch applies the update for one pair (if upd) and emits the partial
+// dot of the next pair (if nxt).
+__global__ void k_twoloop_step(double *v, const double *__restrict__ upd_vec, const double *__restrict__ part_in,
+                               int nin, double rho, double *__restrict__ alpha_store, int second,
+                               const double *__restrict__ alpha_prev, const double *__restrict__ nxt,
+                               double *__restrict__ part_out, int64_t n) {
+  __shared__ double sh[NT];
+  double coef = 0.0;
+  if (upd_vec) {
+    double S = sum_partials<NT>(part_in, nin, sh);
+    if (!second) {
+      double a = rho * S;
+      coef = -a;
+      if (blockIdx.x == 0 && threadIdx.x == 0) *alpha_store = a;
+    } else {
+      coef = *alpha_prev - rho * S;
+    }
+  }
+  double acc = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT) {
+    double vk = v[k];
+    if (upd_vec) {
+      vk += coef * upd_vec[k];
+      v[k] = vk;
+    }
+    if (nxt) acc += nxt[k] * vk;
+  }
+  if (nxt) {
+    acc = block_sum<NT>(acc, sh);
+    if (threadIdx.x == 0) part_out[blockIdx.x] = acc;
+  }
+}
+
+__global__ void k_count_free(const uint8_t *__restrict__ fixed, int64_t n, int *__restrict__ out) {
+  int c = 0;
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT) c += fixed[k] == 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+int grid_for(const Scene &s) { return 2 * s.nsm; }
+}  // namespace
+
+int64_t count_free(Scene &s) {
+  int64_t n = s.nn();
+  if (n == 0) return 0;
+  s.scan.total.ensure(1);
+  HOT_CUDA(cudaMemsetAsync(s.scan.total.p, 0, sizeof(int), s.st));
+  k_count_free<<<grid_for(s), NT, 0, s.st>>>(s.fixed.p, n, s.scan.total.p);
+  HOT_LAUNCH("k_count_free");
+  return read_scan_total(s.scan, s.st);
+}
+
+double dot(Scene &s, const double *x, const double *y, int64_t n) {
+  double o[3];
+  int G = grid_for(s);
+  s.part.ensure(4096);
+  k_dot3<<<G, NT, 0, s.st>>>(x, y, n, 0, s.part.p);
+  HOT_LAUNCH("k_dot3");
+  std::vector<double> h(3 * G);
+  HOT_CUDA(cudaMemcpyAsync(h.data(), s.part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  o[0] = 0.0;
+  for (int b = 0; b < G; ++b) o[0] += h[3 * b];
+  return o[0];
+}
+
+void dots3(Scene &s, const double *x, const double *y, int64_t n, double out[3]) {
+  int G = grid_for(s);
+  s.part.ensure(4096);
+  k_dot3<<<G, NT, 0, s.st>>>(x, y, n, 1, s.part.p);
+  HOT_LAUNCH("k_dot3");
+  std::vector<double> h(3 * G);
+  HOT_CUDA(cudaMemcpyAsync(h.data(), s.part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  out[0] = out[1] = out[2] = 0.0;
+  for (int b = 0; b < G; ++b) {
+    out[0] += h[3 * b];
+    out[1] += h[3 * b + 1];
+    out[2] += h[3 * b + 2];
+  }
+}
+
+void axpy(Scene &s, double *y, double a, const double *x, int64_t n) {
+  k_axpy<<<grid_for(s), NT, 0, s.st>>>(y, a, x, n);
+  HOT_LAUNCH("k_axpy");
+}
+void lincomb(Scene &s, double *z, double a, const double *x, double b, const double *y, int64_t n) {
+  k_lincomb<<<grid_for(s), NT, 0, s.st>>>(z, a, x, b, y, n);
+  HOT_LAUNCH("k_lincomb");
+}
+void scale_copy(Scene &s, double *dst, double a, const double *src, int64_t n) {
+  k_lincomb<<<grid_for(s), NT, 0, s.st>>>(dst, a, src, 0.0, nullptr, n);
+  HOT_LAUNCH("k_lincomb");
+}
+
+// history slot of the k-th newest pair (k = 0 newest)
+static inline int hist_slot(const Scene &s, int k) {
+  int w = s.opts.lbfgs_m;
+  return ((s.hist_head - 1 - k) % w + w) % w;
+}
+
+void two_loop_first(Scene &s, double *q, int64_t n) {
+  const int G = grid_for(s);
+  const int m = s.hist_n;
+  if (m == 0) return;
+  s.part.ensure(4096);
+  s.scal.ensure(64);
+  double *pa = s.part.p, *pb = s.part.p + 2048;
+  // partial of s_newest^T q
+  int sl = hist_slot(s, 0);
+  k_twoloop_step<<<G, NT, 0, s.st>>>(q, nullptr, nullptr, 0, 0.0, nullptr, 0, nullptr, s.hist_s.p + sl * n, pa, n);
+  HOT_LAUNCH("k_twoloop_step");
+  for (int k = 0; k < m; ++k) {
+    int a = hist_slot(s, k);
+    const double *nxt = (k + 1 < m) ? s.hist_s.p + hist_slot(s, k + 1) * n : nullptr;
+    k_twoloop_step<<<G, NT, 0, s.st>>>(q, s.hist_y.p + a * n, pa, G, s.hist_rho[a], s.scal.p + a, 0, nullptr, nxt, pb,
+                                       n);
+    HOT_LAUNCH("k_twoloop_step");
+    std::swap(pa, pb);
+  }
+}
+
+void two_loop_second(Scene &s, double *r, int64_t n) {
+  const int G = grid_for(s);
+  const int m = s.hist_n;
+  if (m == 0) return;
+  double *pa = s.part.p, *pb = s.part.p + 2048;
+  int sl = hist_slot(s, m - 1);
+  k_twoloop_step<<<G, NT, 0, s.st>>>(r, nullptr, nullptr, 0, 0.0, nullptr, 1, nullptr, s.hist_y.p + sl * n, pa, n);
+  HOT_LAUNCH("k_twoloop_step");
+  for (int k = m - 1; k >= 0; --k) {
+    int a = hist_slot(s, k);
+    const double *nxt = (k - 1 >= 0) ? s.hist_y.p + hist_slot(s, k - 1) * n : nullptr;
+    k_twoloop_step<<<G, NT, 0, s.st>>>(r, s.hist_s.p + a * n, pa, G, s.hist_rho[a], nullptr, 1, s.scal.p + a, nxt,
+                                       pb, n);
+    HOT_LAUNCH("k_twoloop_step");
+    std::swap(pa, pb);
+  }
+}
+
+}  // namespace hot

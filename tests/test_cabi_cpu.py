@@ -1,0 +1,50 @@
+"""CPU-side checks of the boundary: the library builds for sm_103a, loads,
+and exports every entry point include/hot_mpm.h declares; the binding's
+struct layouts match the header's sizes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1911_07913_gb300 import build as B
+from paper_1911_07913_gb300 import hot
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hot_mpm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:mpm_status|const char \*)\s*(mpm_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return B.build()
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(hot.EXPORTED)
+
+
+def test_struct_sizes_match_header(lib_path):
+    # sizes follow from the C layout rules on LP64 (x86-64 and aarch64 alike)
+    assert ctypes.sizeof(hot.mpm_material) == 40
+    assert ctypes.sizeof(hot.mpm_bc) == 8 + 12 * 8 + 8
+    assert ctypes.sizeof(hot.mpm_solver_opts) == 8 + 8 * 4 + 3 * 8
+    assert ctypes.sizeof(hot.mpm_step_stats) == 16 + 24 + 8 + 128 + 8
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(hot, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(hot, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        hot.load()

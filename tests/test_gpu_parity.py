@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  Integer work (cell keys, active nodes, Dirichlet flags,
+block patterns) must match bit for bit; floating point within the tolerances
+the method's FP64 arithmetic supports (1e-9 relative on grid velocities after
+a step, 1e-7 relative on particle positions, tighter on single kernels)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import hot_oracle as O
+from paper_1911_07913_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hot():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1911_07913_gb300 import hot as H
+    H.load()
+    return H
+
+
+def make_scenes():
+    bars = scenes.two_bars_scene(seed=3, res=64, width=6, length=14, gap=4, E_a=1e5, E_b=1e8)
+    return {
+        "cube8k_fcr": (scenes.cube_scene(seed=0), scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=2e-3, levels=3)),
+        "bars_nh_cn": (bars, scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3)),
+        "cube_small_l1": (scenes.cube_scene(seed=5, res=16, cube_lo=(5, 4, 5), side=3),
+                          scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=3e-3, levels=1)),
+    }
+
+
+SCENES = make_scenes()
+
+
+def rel(a, b):
+    den = max(np.abs(b).max(), 1e-300)
+    return np.abs(a - b).max() / den
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_p2g_nodes_bit_exact_and_values(hot, name):
+    sc, opts = SCENES[name]
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    gd = g.grid()
+    og = O.p2g(sc)
+    assert np.array_equal(gd["coords"], og.coords.astype(np.int32))
+    assert np.array_equal(gd["fixed"], og.fixed)
+    assert rel(gd["m"], og.m) < 1e-13
+    assert rel(gd["v"], og.v) < 1e-12
+    assert rel(gd["xi"], og.xi) < 1e-13
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_energy_and_gradient(hot, name):
+    sc, opts = SCENES[name]
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, O.step_dt(sc, opts))
+    rng = np.random.default_rng(1)
+    for amp in (0.0, 0.05):
+        dv = amp * rng.normal(size=(prob.n, 3))
+        dv[og.fixed] = 0.0
+        Eg = g.energy(dv)
+        Eo = prob.energy(dv)
+        assert abs(Eg - Eo) <= 1e-12 * max(abs(Eo), 1e-300) + 1e-15
+        gg = g.gradient(dv)
+        go = prob.gradient(dv)
+        assert rel(gg, go) < 1e-11
+
+
+def blocks_of(h):
+    n = h["coords"].shape[0]
+    rows = np.repeat(np.arange(n), np.diff(h["row_ptr"]))
+    M = sp.bsr_matrix((h["vals"], h["cols"], h["row_ptr"]), shape=(3 * n, 3 * n)).tocsr()
+    pat = sp.coo_matrix((np.ones(len(rows)), (rows, h["cols"])), shape=(n, n)).tocsr()
+    return M, pat
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_hierarchy_patterns_exact_values_close(hot, name):
+    sc, opts = SCENES[name]
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    g.build_hierarchy()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, O.step_dt(sc, opts))
+    L = O.build_hierarchy(og.coords, prob.hessian(), prob.hessian_pattern(), opts.levels)
+    for m, lev in enumerate(L):
+        h = g.hessian(m)
+        assert np.array_equal(h["coords"], lev.coords.astype(np.int32)), m
+        M, pat = blocks_of(h)
+        # block pattern bit-exact
+        assert (pat != (lev.pattern > 0)).nnz == 0, m
+        Ho = lev.H.tocsr()
+        scale = np.abs(Ho).max()
+        assert np.abs(M - Ho).max() <= 1e-11 * scale, m
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_vcycle_matches_oracle_with_same_coarse_count(hot, name):
+    sc, opts = SCENES[name]
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    g.build_hierarchy()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, O.step_dt(sc, opts))
+    L = O.build_hierarchy(og.coords, prob.hessian(), prob.hessian_pattern(), opts.levels)
+    rng = np.random.default_rng(2)
+    b = rng.normal(size=(prob.n, 3))
+    u, its = g.vcycle(b)
+    vc = O.VCycle(L, og.fixed, opts.eps, opts.max_coarse_cg)
+    vc.forced = [its]
+    uo = vc(b)
+    assert rel(u, uo) < 1e-9
+    # the GPU's own stopping rule agrees with the oracle's
+    vc2 = O.VCycle(L, og.fixed, opts.eps, opts.max_coarse_cg)
+    vc2(b)
+    assert abs(vc2.cg_counts[0] - its) <= 1
+
+
+def replay_trace(tr):
+    return O.Trace(iters=tr["iters"], alphas=tr["alphas"], ls_trials=tr["ls_trials"],
+                   cg_counts=tr["cg_counts"], skipped=tr["skipped"], fallback=tr["fallback"])
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_full_step_replay_parity(hot, name):
+    sc, opts = SCENES[name]
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    st = g.solve()
+    gd = g.grid()
+    tr = g.trace()
+    g.g2p()
+    out = g.get_state()
+    ref, info = O.hot_step(sc, opts, replay=replay_trace(tr))
+    assert st["status"] == 0 and st["iters"] == tr["iters"] >= 1
+    vg = gd["v"] + gd["dv"]
+    assert rel(vg, info["v_new"]) < 1e-9
+    assert rel(out["x"], ref.x) < 1e-7
+    assert rel(out["v"], ref.v) < 1e-9
+    assert rel(out["F"], ref.F) < 1e-9
+    # the GPU stopped where the oracle's own test says converged
+    prob = info["problem"]
+    gr = prob.gradient(gd["dv"])
+    if opts.cn_mode == 0:
+        nrm, nfree = prob.cn_norm(gr)
+        assert nrm <= opts.eps * np.sqrt(nfree) * (1 + 1e-6)
+    else:
+        g1 = prob.gradient(np.zeros_like(gd["dv"]))
+        assert np.linalg.norm(gr) <= opts.eps * np.linalg.norm(g1) * (1 + 1e-6)
+
+
+def test_free_running_decisions_match(hot):
+    sc, opts = SCENES["cube8k_fcr"]
+    g = hot.HotScene(sc, opts)
+    st = g.step()
+    tr = g.trace()
+    ref, info = O.hot_step(sc, opts)
+    assert info["trace"].iters == tr["iters"]
+    assert info["trace"].cg_counts == tr["cg_counts"]
+    assert rel(g.get_state()["v"], ref.v) < 1e-9
+    del st
+
+
+@pytest.mark.parametrize("name", ["cube8k_fcr", "bars_nh_cn"])
+def test_mixed_precision_converges_to_same_tolerance(hot, name):
+    sc, opts = SCENES[name]
+    mixed = scenes.SolverOptions(**{**opts.__dict__, "precision": 1})
+    g = hot.HotScene(sc, mixed)
+    g.p2g()
+    st = g.solve()
+    gd = g.grid()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, st["dt"])
+    gr = prob.gradient(gd["dv"])
+    if opts.cn_mode == 0:
+        nrm, nfree = prob.cn_norm(gr)
+        assert nrm <= opts.eps * np.sqrt(nfree) * (1 + 1e-6)
+    else:
+        g1 = prob.gradient(np.zeros_like(gd["dv"]))
+        assert np.linalg.norm(gr) <= opts.eps * np.linalg.norm(g1) * (1 + 1e-6)
+    # FP32 Hessian against the FP64 oracle
+    g.build_hierarchy()
+    H = g.hessian(0)
+    M, _ = blocks_of(H)
+    Ho = prob.hessian().tocsr()
+    assert np.abs(M - Ho).max() <= 1e-5 * np.abs(Ho).max()
+
+
+def test_empty_scene(hot):
+    sc = scenes.cube_scene(seed=0).subset(np.arange(0))
+    g = hot.HotScene(sc, scenes.SolverOptions(dt=1e-3))
+    st = g.step()
+    assert st["status"] == 0 and st["iters"] == 0
+    assert g.grid()["coords"].shape == (0, 3)
+
+
+def test_particle_on_cell_centre_gives_zero_mass_nodes(hot):
+    sc = scenes.cube_scene(seed=0, res=16, cube_lo=(6, 6, 6), side=1)
+    dx = sc.dx
+    sc = sc.subset(np.arange(1))
+    sc.x[0] = np.array([7.5, 7.5, 7.5]) * dx
+    opts = scenes.SolverOptions(eps=1e-8, cn_mode=1, dt=1e-3, levels=2)
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    gd = g.grid()
+    og = O.p2g(sc)
+    assert np.array_equal(gd["fixed"], og.fixed)
+    assert (gd["m"] == 0).sum() == (og.m == 0).sum() > 0
+    st = g.solve()
+    assert st["status"] == 0
+
+
+def test_domain_error_is_reported(hot):
+    sc = scenes.cube_scene(seed=0, res=16, cube_lo=(5, 5, 5), side=2)
+    sc.x[3] = np.array([0.01, 0.5, 0.5])
+    g = hot.HotScene(sc, scenes.SolverOptions(dt=1e-3))
+    with pytest.raises(hot.HotError) as e:
+        g.p2g()
+    assert e.value.code == 9
+
+
+def test_state_round_trip_and_order(hot):
+    sc, opts = SCENES["cube_small_l1"]
+    g = hot.HotScene(sc, opts)
+    s0 = g.get_state()
+    assert np.array_equal(s0["x"], sc.x) and np.array_equal(s0["F"], sc.F)
+    g.step()
+    g.step()
+    s2 = g.get_state()
+    g.set_state(x=s2["x"] + 0.0)
+    assert np.array_equal(g.get_state()["x"], s2["x"])
