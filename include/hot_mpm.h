@@ -109,6 +109,8 @@ typedef struct {
   double dt;             /* > 0: fixed step; else min(1/fps, cfl dx / v_max) */
   double fps;
   double cfl;
+  int32_t flags;         /* bit 0: run the V-cycle eagerly instead of as a CUDA graph */
+  int32_t reserved;
 } mpm_solver_opts;
 
 typedef struct {
@@ -124,6 +126,8 @@ typedef struct {
   int64_t nnz_blocks[8];   /* 3x3 blocks per level */
   int32_t n_levels;
   int32_t status;
+  int32_t graph_vcycles;   /* V-cycles replayed from a captured CUDA graph */
+  int32_t reserved;
 } mpm_step_stats;
 
 /* Device memory hook.  alloc(bytes, stream, ctx) returns device memory or
@@ -206,6 +210,19 @@ mpm_status mpm_apply_vcycle(mpm_scene_t s, const double *b, double *u, int32_t *
 mpm_status mpm_get_trace(mpm_scene_t s, int32_t capacity, int32_t *n_iters, double *alphas,
                          int32_t *ls_trials, int32_t *skipped, int32_t *fallback,
                          int32_t *n_vcycles, int32_t *cg_counts);
+
+/* Per-kernel device timing.  mpm_profile(s, 1, only) clears and starts
+ * recording CUDA events on the scene's stream around the library's main
+ * kernels (only the kernel named `only` when it is not NULL);
+ * mpm_profile(s, 0, NULL) stops.  mpm_profile_read returns, per kernel name (32
+ * bytes each in `names`), the summed event time in ms and the launch count;
+ * *count gets the number of names (entries beyond capacity are dropped). */
+mpm_status mpm_profile(mpm_scene_t s, int32_t enable, const char *only);
+mpm_status mpm_profile_read(mpm_scene_t s, int32_t capacity, int32_t *count, char *names, double *total_ms,
+                            int64_t *launches);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t mpm_kernel_launch_count(void);
 
 /* Device bytes held by the scene (its admission footprint). */
 mpm_status mpm_scene_footprint(mpm_scene_t s, int64_t *bytes);

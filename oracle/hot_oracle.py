@@ -697,12 +697,17 @@ def hot_solve(prob: Problem, opts, replay: Optional[Trace] = None, levels=None):
         fb = 0
         if replay is not None:
             fb = replay.fallback[it]
-        elif float(np.sum(p * g)) >= 0.0:
+        elif not float(np.sum(p * g)) < 0.0:
             fb = 1
         if fb:
-            # READING: a non-descent direction restarts from the V-cycle alone
+            # READING: a non-descent direction restarts from the V-cycle alone,
+            # and from steepest descent if that is not a descent direction
             hist = []
             p = vc(-g)
+            if replay is None and not float(np.sum(p * g)) < 0.0:
+                fb = 2
+            if fb == 2:
+                p = -g
         tr.fallback.append(fb)
         forced = replay.alphas[it] if replay is not None else None
         alpha, E1, trials = line_search(prob, dv, p, E, opts.max_ls, forced)

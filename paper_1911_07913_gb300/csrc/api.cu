@@ -4,6 +4,7 @@
 // termination, line-search acceptance, L-BFGS pair acceptance); every vector
 // and particle operation runs on the device.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -17,7 +18,47 @@ static mpm_alloc_fn g_alloc = nullptr;
 static mpm_free_fn g_free = nullptr;
 static void *g_ctx = nullptr;
 
+static std::atomic<long long> g_launches{0};
+
 void fail(mpm_status code, const std::string &msg) { throw Error{code, msg}; }
+
+void note_launch(const char *what) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  check_cuda(cudaGetLastError(), what);
+}
+
+static cudaEvent_t take_event(Scene &s) {
+  if (!s.ev_pool.empty()) {
+    cudaEvent_t e = s.ev_pool.back();
+    s.ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  HOT_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+ProfScope::ProfScope(Scene &sc, const char *name) : s(&sc), id(-1) {
+  if (!sc.prof) return;
+  if (!sc.prof_only.empty() && sc.prof_only != name) return;
+  for (size_t k = 0; k < sc.prof_names.size(); ++k)
+    if (sc.prof_names[k] == name) id = (int)k;
+  if (id < 0) {
+    id = (int)sc.prof_names.size();
+    sc.prof_names.push_back(name);
+  }
+  a = take_event(sc);
+  b = take_event(sc);
+  HOT_CUDA(cudaEventRecord(a, sc.st));
+}
+
+ProfScope::~ProfScope() {
+  if (id < 0) return;
+  cudaEventRecord(b, s->st);
+  s->prof_ids.push_back(id);
+  s->prof_ev.push_back(a);
+  s->prof_ev.push_back(b);
+}
 
 void check_cuda(cudaError_t e, const char *what) {
   if (e != cudaSuccess) {
@@ -81,6 +122,10 @@ void Scene::release() {
   for (auto &t : topo) t.release();
   hd.release();
   hf.release();
+  for (auto e : prof_ev) cudaEventDestroy(e);
+  for (auto e : ev_pool) cudaEventDestroy(e);
+  prof_ev.clear();
+  ev_pool.clear();
 }
 
 namespace {
@@ -109,6 +154,7 @@ void compute_dt(Scene &s) {
 }
 
 void do_p2g(Scene &s) {
+  s.drop_graph();
   HOT_CUDA(cudaMemsetAsync(s.errflag.p, 0, sizeof(int), s.st));
   compute_dt(s);
   if (s.np > 0) {
@@ -150,15 +196,22 @@ void build_hier(Scene &s, Hier<T> &h) {
 
 void do_build(Scene &s) {
   if (s.phase < PH_P2G) fail(MPM_ERR_STATE, "mpm_p2g must run before the hierarchy is built");
+  s.drop_graph();
   if (s.opts.precision == 0) build_hier<double>(s, s.hd);
   else build_hier<float>(s, s.hf);
   s.phase = PH_HIER;
 }
 
-int run_vcycle(Scene &s, const double *b, double *u) {
-  int its = s.opts.precision == 0 ? vcycle<double>(s, s.hd, b, u, -1) : vcycle<float>(s, s.hf, b, u, -1);
-  s.trace.cg_counts.push_back(its);
-  return its;
+void run_vcycle(Scene &s, const double *b, double *u, bool use_graph) {
+  if (s.opts.precision == 0) vcycle<double>(s, s.hd, b, u, use_graph);
+  else vcycle<float>(s, s.hf, b, u, use_graph);
+}
+void reset_log(Scene &s) {
+  if (s.opts.precision == 0) reset_cg_log<double>(s, s.hd);
+  else reset_cg_log<float>(s, s.hf);
+}
+std::vector<int> read_log(Scene &s) {
+  return s.opts.precision == 0 ? read_cg_log<double>(s, s.hd) : read_cg_log<float>(s, s.hf);
 }
 
 mpm_status do_solve(Scene &s, mpm_step_stats *st) {
@@ -175,6 +228,8 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   HOT_CUDA(cudaMemsetAsync(s.errflag.p, 0, sizeof(int), s.st));
   velocity_gradient(s, s.v.p, nullptr, s.Lv.p);
   s.trace.clear();
+  s.graph_launches = 0;
+  reset_log(s);
   s.hist_n = 0;
   s.hist_head = 0;
   const int64_t nfree = count_free(s);
@@ -206,15 +261,22 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
     // two-loop recursion around the V-cycle initializer (Alg. 3)
     scale_copy(s, s.q.p, -1.0, s.g.p, n3);
     two_loop_first(s, s.q.p, n3);
-    cg_total += run_vcycle(s, s.q.p, s.pdir.p);
+    run_vcycle(s, s.q.p, s.pdir.p, true);
     two_loop_second(s, s.pdir.p, n3);
     int fb = 0;
-    if (dot(s, s.pdir.p, s.g.p, n3) >= 0.0) {
+    double pg = dot(s, s.pdir.p, s.g.p, n3);
+    if (!(pg < 0.0)) {
       // not a descent direction: drop the history, use the V-cycle alone
       fb = 1;
       s.hist_n = 0;
       scale_copy(s, s.q.p, -1.0, s.g.p, n3);
-      cg_total += run_vcycle(s, s.q.p, s.pdir.p);
+      run_vcycle(s, s.q.p, s.pdir.p, true);
+      pg = dot(s, s.pdir.p, s.g.p, n3);
+      if (!(pg < 0.0)) {
+        // still none (or not finite): steepest descent
+        fb = 2;
+        scale_copy(s, s.pdir.p, -1.0, s.g.p, n3);
+      }
     }
     s.trace.fallback.push_back(fb);
     // backtracking line search on E(dv + alpha p)
@@ -261,6 +323,8 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   }
   int e = read_errflag(s);
   if (e & DEV_ERR_TIMEOUT) status = MPM_ERR_TIMEOUT;
+  s.trace.cg_counts = read_log(s);
+  for (int c : s.trace.cg_counts) cg_total += c > 0 ? c : 0;
   s.trace.iters = it;
   s.phase = PH_SOLVED;
   s.has_solution = true;
@@ -280,6 +344,7 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
     out.nnz_blocks[m] = s.topo[m].nnzb;
   }
   out.status = status;
+  out.graph_vcycles = s.graph_launches;
   s.last_stats = out;
   if (st) *st = out;
   return status;
@@ -382,7 +447,13 @@ mpm_status mpm_create_scene(const mpm_scene_desc *d, const mpm_solver_opts *o, m
         s->gravity[k] = d->gravity[k];
       }
       s->ncell_dense = (int64_t)s->geo.nb[0] * s->geo.nb[1] * s->geo.nb[2] * 64;
-      s->set_stream((cudaStream_t)d->cuda_stream);
+      cudaStream_t st = (cudaStream_t)d->cuda_stream;
+      if (st == nullptr) {
+        // a private stream: the legacy default stream cannot be captured into graphs
+        HOT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        s->own_stream = true;
+      }
+      s->set_stream(st);
       int dev = 0;
       HOT_CUDA(cudaGetDevice(&dev));
       HOT_CUDA(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -430,6 +501,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc *d, const mpm_solver_opts *o, m
       HOT_CUDA(cudaStreamSynchronize(s->st));
     } catch (...) {
       s->release();
+      if (s->own_stream) cudaStreamDestroy(s->st);
       delete s;
       throw;
     }
@@ -442,7 +514,9 @@ mpm_status mpm_destroy_scene(mpm_scene_t sc) {
   if (!sc) return MPM_OK;
   Scene *s = reinterpret_cast<Scene *>(sc);
   cudaStreamSynchronize(s->st);
+  s->drop_graph();
   s->release();
+  if (s->own_stream) cudaStreamDestroy(s->st);
   delete s;
   return MPM_OK;
 }
@@ -649,11 +723,12 @@ mpm_status mpm_apply_vcycle(mpm_scene_t sc, const double *b, double *u, int32_t 
     s->g_e.ensure(n3 + 3);
     HOT_CUDA(cudaMemsetAsync(s->errflag.p, 0, sizeof(int), s->st));
     HOT_CUDA(cudaMemcpyAsync(s->dv_e.p, b, sizeof(double) * n3, cudaMemcpyHostToDevice, s->st));
-    int its = s->opts.precision == 0 ? vcycle<double>(*s, s->hd, s->dv_e.p, s->g_e.p, -1)
-                                     : vcycle<float>(*s, s->hf, s->dv_e.p, s->g_e.p, -1);
+    reset_log(*s);
+    run_vcycle(*s, s->dv_e.p, s->g_e.p, false);
     HOT_CUDA(cudaMemcpyAsync(u, s->g_e.p, sizeof(double) * n3, cudaMemcpyDeviceToHost, s->st));
     HOT_CUDA(cudaStreamSynchronize(s->st));
-    if (cg_iters) *cg_iters = its;
+    std::vector<int> lg = read_log(*s);
+    if (cg_iters) *cg_iters = lg.empty() ? 0 : lg.back();
     if (read_errflag(*s) & DEV_ERR_TIMEOUT) fail(MPM_ERR_TIMEOUT, "coarse solve barrier timed out");
     return MPM_OK;
   });
@@ -684,6 +759,53 @@ mpm_status mpm_get_trace(mpm_scene_t sc, int32_t capacity, int32_t *n_iters, dou
     return MPM_OK;
   });
 }
+
+mpm_status mpm_profile(mpm_scene_t sc, int32_t enable, const char *only) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    HOT_CUDA(cudaStreamSynchronize(s->st));
+    if (enable) {
+      for (auto e : s->prof_ev) s->ev_pool.push_back(e);
+      s->prof_ev.clear();
+      s->prof_ids.clear();
+      s->prof_names.clear();
+    }
+    s->prof = enable != 0;
+    s->prof_only = only ? only : "";
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_profile_read(mpm_scene_t sc, int32_t capacity, int32_t *count, char *names, double *total_ms,
+                            int64_t *launches) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s || !count) fail(MPM_ERR_INVALID_ARG, "NULL argument");
+    HOT_CUDA(cudaStreamSynchronize(s->st));
+    const int nk = (int)s->prof_names.size();
+    std::vector<double> ms(nk, 0.0);
+    std::vector<int64_t> cnt(nk, 0);
+    for (size_t k = 0; k < s->prof_ids.size(); ++k) {
+      float t = 0.f;
+      HOT_CUDA(cudaEventElapsedTime(&t, s->prof_ev[2 * k], s->prof_ev[2 * k + 1]));
+      ms[s->prof_ids[k]] += t;
+      cnt[s->prof_ids[k]] += 1;
+    }
+    *count = nk;
+    for (int k = 0; k < nk && k < capacity; ++k) {
+      if (names) {
+        std::memset(names + 32 * k, 0, 32);
+        std::strncpy(names + 32 * k, s->prof_names[k].c_str(), 31);
+      }
+      if (total_ms) total_ms[k] = ms[k];
+      if (launches) launches[k] = cnt[k];
+    }
+    return MPM_OK;
+  });
+}
+
+int64_t mpm_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
 
 mpm_status mpm_scene_footprint(mpm_scene_t sc, int64_t *bytes) {
   Scene *s = reinterpret_cast<Scene *>(sc);

@@ -23,8 +23,9 @@ struct Error {
 };
 [[noreturn]] void fail(mpm_status code, const std::string &msg);
 void check_cuda(cudaError_t e, const char *what);
+void note_launch(const char *what);   // error check + launch counter
 #define HOT_CUDA(x) ::hot::check_cuda((x), #x)
-#define HOT_LAUNCH(what) ::hot::check_cuda(cudaGetLastError(), what)
+#define HOT_LAUNCH(what) ::hot::note_launch(what)
 
 // device-side status bits written by kernels, read by the host
 enum : int {

@@ -373,6 +373,7 @@ __global__ void k_hessian_finish(int64_t nn, const int *__restrict__ row_ptr, co
 
 void velocity_gradient(Scene &s, const double *u, const double *u2, double *L) {
   if (s.np == 0) return;
+  ProfScope prof_(s, "velgrad");
   k_velgrad<<<(unsigned)((s.np + NT - 1) / NT), NT, 0, s.st>>>(s.pd.p, s.np, geo(s), s.topo[0].map.p, u, u2, L);
   HOT_LAUNCH("k_velgrad");
 }
@@ -384,6 +385,7 @@ double energy(Scene &s, const double *L1, const double *L2, double alpha, const 
     L2 = nullptr;
     pv = nullptr;
   }
+  ProfScope prof_(s, "energy");
   k_energy<<<nbp + nbn, NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, L1, L2, alpha, s.dt, nbp, s.nn(), s.m.p,
                                        dvv, pv, s.gravity[0], s.gravity[1], s.gravity[2], s.part.p);
   HOT_LAUNCH("k_energy");
@@ -399,6 +401,7 @@ void gradient(Scene &s, const double *Lcur, const double *dvec, double *gout, do
   const int64_t nn = s.nn();
   HOT_CUDA(cudaMemsetAsync(gout, 0, sizeof(double) * 3 * nn, s.st));
   if (s.n_blocks > 0) {
+    ProfScope prof_(s, "grad_scatter");
     k_grad_scatter<<<(unsigned)s.n_blocks, NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, Lcur, s.dt,
                                                           s.blk_first.p, s.blk_end.p, s.blk_key.p, geo(s),
                                                           s.topo[0].map.p, gout);
@@ -424,6 +427,7 @@ template <class T>
 void particle_stiffness(Scene &s, Hier<T> &h) {
   h.A45.ensure((size_t)45 * s.np, 1.0);
   if (s.np == 0) return;
+  ProfScope prof_(s, "stiffness");
   k_stiffness<T><<<(unsigned)((s.np + 127) / 128), 128, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, s.Lv.p,
                                                                   s.dt, h.A45.p);
   HOT_LAUNCH("k_stiffness");
@@ -436,6 +440,7 @@ void hessian_assemble(Scene &s, Hier<T> &h) {
   L.vals.ensure(9 * (size_t)t.nnzb);
   HOT_CUDA(cudaMemsetAsync(L.vals.p, 0, sizeof(T) * 9 * t.nnzb, s.st));
   if (s.n_cells > 0) {
+    ProfScope prof_(s, "hessian_cells");
     k_hessian_cells<T><<<(unsigned)s.n_cells, HNT, 0, s.st>>>(s.pd.p, s.np, h.A45.p, s.cell_first.p, s.cell_n.p,
                                                              s.cell_key.p, geo(s), s.dt, t.map.p, t.row_ptr.p,
                                                              t.slotpos.p, L.vals.p);

@@ -71,24 +71,24 @@ struct Hier {
   DBuf<T> x, r, z, p, Ap;              // coarsest PCG vectors
   DBuf<double> part;                   // PCG partial sums
   DBuf<unsigned int> bar;              // grid barrier words
-  DBuf<int> info;                      // PCG iteration count / status
+  DBuf<int> cg_log;                    // PCG iteration counts; last entry = count
   void set_stream(cudaStream_t st) {
     for (auto &l : L) l.set_stream(st);
     A45.st = x.st = r.st = z.st = p.st = Ap.st = st;
     part.st = st;
     bar.st = st;
-    info.st = st;
+    cg_log.st = st;
   }
   size_t bytes() const {
     size_t b = A45.bytes() + x.bytes() + r.bytes() + z.bytes() + p.bytes() + Ap.bytes() +
-               part.bytes() + bar.bytes() + info.bytes();
+               part.bytes() + bar.bytes() + cg_log.bytes();
     for (auto &l : L) b += l.bytes();
     return b;
   }
   void release() {
     for (auto &l : L) l.release();
     A45.release(); x.release(); r.release(); z.release(); p.release(); Ap.release();
-    part.release(); bar.release(); info.release();
+    part.release(); bar.release(); cg_log.release();
   }
 };
 
@@ -102,6 +102,17 @@ struct Trace {
     iters = 0;
     alphas.clear(); ls_trials.clear(); skipped.clear(); fallback.clear(); cg_counts.clear();
   }
+};
+
+struct Scene;
+// Opt-in device timing of one kernel launch (CUDA events on the scene's
+// stream around the launch); no cost when the scene's profiling is off.
+struct ProfScope {
+  Scene *s;
+  int id;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(Scene &sc, const char *name);
+  ~ProfScope();
 };
 
 struct Scene {
@@ -163,6 +174,25 @@ struct Scene {
   Trace trace;
   mpm_step_stats last_stats;
 
+  // the V-cycle as a CUDA graph (re-captured whenever the hierarchy changes)
+  bool graphs_ok = true;
+  int graph_launches = 0;
+  bool own_stream = false;
+  cudaGraphExec_t vgraph = nullptr;
+  const void *vgraph_b = nullptr, *vgraph_u = nullptr;
+  void drop_graph() {
+    if (vgraph) cudaGraphExecDestroy(vgraph);
+    vgraph = nullptr;
+  }
+
+  // per-kernel device timing
+  bool prof = false;
+  std::string prof_only;                // record only this kernel name when non-empty
+  std::vector<std::string> prof_names;
+  std::vector<int> prof_ids;
+  std::vector<cudaEvent_t> prof_ev;     // start/stop pairs, in launch order
+  std::vector<cudaEvent_t> ev_pool;
+
   int64_t nn() const { return topo[0].n; }
   void set_stream(cudaStream_t s) {
     st = s;
@@ -219,10 +249,14 @@ template <class T>
 void rap(Scene &s, Hier<T> &h, int m);          // numeric H^{m+1} = R H^m R^T
 template <class T>
 void finalize_values(Scene &s, Hier<T> &h, int m);   // diagonal inverses
-// Alg. 2 on b_in (3n doubles, level 0) -> u_out; returns the coarsest PCG
-// iteration count (forced_cg >= 0 imposes that count)
+// Alg. 2 on b_in (3n doubles, level 0) -> u_out, asynchronous; the coarsest
+// PCG appends its iteration count to a device log
 template <class T>
-int vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, int forced_cg);
+void vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, bool use_graph);
+template <class T>
+void reset_cg_log(Scene &s, Hier<T> &h);
+template <class T>
+std::vector<int> read_cg_log(Scene &s, Hier<T> &h);
 
 // ---- vecops.cu (deterministic: fixed grid, fixed-order partial sums)
 double dot(Scene &s, const double *x, const double *y, int64_t n);

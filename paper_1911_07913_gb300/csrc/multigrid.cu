@@ -225,7 +225,12 @@ __global__ void __launch_bounds__(128) k_rap(int64_t nc, const int *__restrict__
   }
 }
 
-// inverse of each diagonal block and the scalar diagonal
+// Inverse of each diagonal block (formed in float64) and the scalar diagonal.
+// A block that is not safely positive definite in the level's precision (its
+// Cholesky pivots fail, or in float32 the smallest pivot is below 1e-6 of the
+// largest, where rounding of a stiffness-dominated block swamps the mass
+// term) is shifted by a multiple of its mean diagonal until it is.  In float64
+// the assembled blocks are positive definite and the shift stays zero.
 template <class T>
 __global__ void k_diag(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ slotpos,
                        const T *__restrict__ vals, T *__restrict__ dinv, T *__restrict__ diag) {
@@ -233,21 +238,44 @@ __global__ void k_diag(int64_t n, const int *__restrict__ row_ptr, const int *__
   if (i >= n) return;
   int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
   int pos = slotpos[i * NSLOT + DIAG_SLOT] - rp;
-  T D[9];
+  double D[9];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) D[e] = vals[9 * (int64_t)rp + e * nb + pos];
-  T c[9];
+  for (int e = 0; e < 9; ++e) D[e] = (double)vals[9 * (int64_t)rp + e * nb + pos];
+  const double mean = fabs(D[0] + D[4] + D[8]) / 3.0 + 1e-300;
+  const double ratio = sizeof(T) == 4 ? 1e-6 : 0.0;
+  double shift = 0.0;
+  for (int attempt = 0; attempt < 12; ++attempt) {
+    // Cholesky pivots of the symmetric part of D + shift I
+    double a00 = D[0] + shift, a11 = D[4] + shift, a22 = D[8] + shift;
+    double a01 = 0.5 * (D[1] + D[3]), a02 = 0.5 * (D[2] + D[6]), a12 = 0.5 * (D[5] + D[7]);
+    double p0 = a00;
+    bool ok = p0 > 0.0;
+    double l10 = ok ? a01 / p0 : 0.0, l20 = ok ? a02 / p0 : 0.0;
+    double p1 = a11 - l10 * a01;
+    ok = ok && p1 > 0.0;
+    double l21 = ok ? (a12 - l20 * a01) / p1 : 0.0;
+    double p2 = a22 - l20 * a02 - l21 * l21 * p1;
+    ok = ok && p2 > 0.0;
+    if (ok) {
+      double pmax = fmax(p0, fmax(p1, p2)), pmin = fmin(p0, fmin(p1, p2));
+      if (pmin >= ratio * pmax) break;
+    }
+    shift = (shift == 0.0 ? (sizeof(T) == 4 ? 1e-6 : 1e-12) : 10.0 * shift / mean) * mean;
+  }
+  D[0] += shift;
+  D[4] += shift;
+  D[8] += shift;
+  double c[9];
   cofactor3(D, c);
-  T det = D[0] * c[0] + D[1] * c[1] + D[2] * c[2];
-  T inv = T(1) / det;
+  double inv = 1.0 / (D[0] * c[0] + D[1] * c[1] + D[2] * c[2]);
   // inverse = cof^T / det
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) dinv[9 * i + 3 * a + b] = c[3 * b + a] * inv;
-  diag[3 * i] = D[0];
-  diag[3 * i + 1] = D[4];
-  diag[3 * i + 2] = D[8];
+    for (int b = 0; b < 3; ++b) dinv[9 * i + 3 * a + b] = (T)(c[3 * b + a] * inv);
+  diag[3 * i] = (T)D[0];
+  diag[3 * i + 1] = (T)D[4];
+  diag[3 * i + 2] = (T)D[8];
 }
 
 // 27-coloring c = (x mod 3) + 3 (y mod 3) + 9 (z mod 3)
@@ -266,25 +294,37 @@ __global__ void k_color_fill(int64_t n, const int *__restrict__ coords, int *__r
 }
 
 // ---------------------------------------------------------------------------
-// smoothing and transfer kernels (one warp per row)
+// smoothing kernels: a group of RL consecutive lanes per row.  Lanes of a
+// group read consecutive blocks of the row (entry-major storage keeps each of
+// the 9 entry streams contiguous), then the group reduces its 3 sums with
+// log2(RL) shuffles.
 // ---------------------------------------------------------------------------
+constexpr int RL = 32;
+constexpr int RPW = 32 / RL;   // rows per warp
+
 template <class T>
-__device__ __forceinline__ void row_product(int64_t i, int lane, const int *__restrict__ row_ptr,
+__device__ __forceinline__ void row_product(int64_t i, bool valid, int lane, const int *__restrict__ row_ptr,
                                             const int *__restrict__ cols, const T *__restrict__ vals,
                                             const T *u, bool skip_diag, T acc[3]) {
-  const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
-  const T *v = vals + 9 * (int64_t)rp;
   acc[0] = acc[1] = acc[2] = T(0);
-  for (int b = lane; b < nb; b += 32) {
-    int j = cols[rp + b];
-    if (skip_diag && j == i) continue;
-    T u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
-    acc[0] += v[b] * u0 + v[nb + b] * u1 + v[2 * nb + b] * u2;
-    acc[1] += v[3 * nb + b] * u0 + v[4 * nb + b] * u1 + v[5 * nb + b] * u2;
-    acc[2] += v[6 * nb + b] * u0 + v[7 * nb + b] * u1 + v[8 * nb + b] * u2;
+  if (valid) {
+    const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
+    const T *v = vals + 9 * (int64_t)rp;
+#pragma unroll 2
+    for (int b = lane; b < nb; b += RL) {
+      int j = cols[rp + b];
+      T h[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) h[e] = v[e * nb + b];
+      if (skip_diag && j == i) continue;
+      T u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
+      acc[0] += h[0] * u0 + h[1] * u1 + h[2] * u2;
+      acc[1] += h[3] * u0 + h[4] * u1 + h[5] * u2;
+      acc[2] += h[6] * u0 + h[7] * u1 + h[8] * u2;
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = RL / 2; o > 0; o >>= 1) {
     acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
     acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
     acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
@@ -296,12 +336,14 @@ template <class T>
 __global__ void k_sgs_color(const int *__restrict__ list, int nrows, const int *__restrict__ row_ptr,
                             const int *__restrict__ cols, const T *__restrict__ vals, const T *__restrict__ dinv,
                             const T *__restrict__ b, T *u) {
-  int w = blockIdx.x * WPB + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= nrows) return;
-  int64_t i = list[w];
+  const int warp = blockIdx.x * WPB + (threadIdx.x >> 5);
+  if (warp * RPW >= nrows) return;   // warp-uniform
+  const int g = warp * RPW + ((threadIdx.x & 31) / RL), lane = threadIdx.x % RL;
+  const bool valid = g < nrows;
+  const int64_t i = valid ? list[g] : 0;
   T acc[3];
-  row_product<T>(i, lane, row_ptr, cols, vals, u, true, acc);
-  if (lane == 0) {
+  row_product<T>(i, valid, lane, row_ptr, cols, vals, u, true, acc);
+  if (valid && lane == 0) {
     T y0 = b[3 * i] - acc[0], y1 = b[3 * i + 1] - acc[1], y2 = b[3 * i + 2] - acc[2];
     const T *D = dinv + 9 * i;
     u[3 * i] = D[0] * y0 + D[1] * y1 + D[2] * y2;
@@ -315,12 +357,14 @@ template <class T>
 __global__ void k_residual(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ cols,
                            const T *__restrict__ vals, const T *__restrict__ b, const T *__restrict__ u,
                            T *__restrict__ r) {
-  int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
-  int lane = threadIdx.x & 31;
-  if (i >= n) return;
+  const int64_t warp = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+  if (warp * RPW >= n) return;
+  const int64_t i = warp * RPW + ((threadIdx.x & 31) / RL);
+  const int lane = threadIdx.x % RL;
+  const bool valid = i < n;
   T acc[3];
-  row_product<T>(i, lane, row_ptr, cols, vals, u, false, acc);
-  if (lane == 0) {
+  row_product<T>(i, valid, lane, row_ptr, cols, vals, u, false, acc);
+  if (valid && lane == 0) {
     r[3 * i] = b[3 * i] - acc[0];
     r[3 * i + 1] = b[3 * i + 1] - acc[1];
     r[3 * i + 2] = b[3 * i + 2] - acc[2];
@@ -437,8 +481,8 @@ template <class T>
 __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ cols,
                                                    const T *__restrict__ vals, const T *__restrict__ diag,
                                                    const T *__restrict__ b, T *x, T *r, T *z, T *p, T *Ap,
-                                                   double *part, unsigned *bar, int *info, int *err, double tau,
-                                                   int max_iter, int forced) {
+                                                   double *part, unsigned *bar, int *log, int *log_idx, int log_cap,
+                                                   int *err, double tau, int max_iter) {
   __shared__ double sh[NT];
   unsigned gen = 0;
   const int64_t n3 = 3 * n;
@@ -461,21 +505,21 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
   if (!grid_sync(bar, gen, err)) return;
   double rz = sum_partials<NT>(partA, G, sh);
   const double bn = sqrt(fmax(rz, 0.0));
-  const double kk = fmin(0.5, sqrt(fmax(bn, tau)));
+  // in float32 a relative residual below ~1e-3 is not reliably reachable;
+  // the floor keeps the (preconditioning) coarse solve from running to its cap
+  const double kk = fmax(fmin(0.5, sqrt(fmax(bn, tau))), sizeof(T) == 4 ? 1e-3 : 0.0);
   int it = 0;
   while (true) {
-    if (forced >= 0) {
-      if (it >= forced) break;
-    } else if (sqrt(fmax(rz, 0.0)) <= kk * bn || it >= max_iter) {
-      break;
-    }
+    if (sqrt(fmax(rz, 0.0)) <= kk * bn || it >= max_iter) break;
     // Ap = H p, partial p^T Ap
     acc = 0.0;
-    const int warps = G * (NT / 32);
-    for (int64_t i = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); i < n; i += warps) {
+    const int64_t warps = (int64_t)G * (NT / 32);
+    for (int64_t w0 = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); w0 * RPW < n; w0 += warps) {
+      const int64_t i = w0 * RPW + ((threadIdx.x & 31) / RL);
+      const bool valid = i < n;
       T a3[3];
-      row_product<T>(i, threadIdx.x & 31, row_ptr, cols, vals, p, false, a3);
-      if ((threadIdx.x & 31) == 0) {
+      row_product<T>(i, valid, threadIdx.x % RL, row_ptr, cols, vals, p, false, a3);
+      if (valid && (threadIdx.x % RL) == 0) {
         Ap[3 * i] = a3[0];
         Ap[3 * i + 1] = a3[1];
         Ap[3 * i + 2] = a3[2];
@@ -509,7 +553,11 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
     ++it;
     if (!grid_sync(bar, gen, err)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = it;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int k = *log_idx;
+    if (k < log_cap) log[k] = it;
+    *log_idx = k + 1;
+  }
 }
 
 template <class T>
@@ -619,6 +667,7 @@ void rap(Scene &s, Hier<T> &h, int m) {
   Vals<T> &VC = h.L[m + 1];
   VC.vals.ensure(9 * (size_t)C.nnzb + 9);
   if (C.n == 0) return;
+  ProfScope prof_(s, "rap");
   k_rap<T><<<(unsigned)C.n, 128, 0, s.st>>>(C.n, C.coords.p, C.row_ptr.p, C.slotpos.p, VC.vals.p, F.map.p, dims_of(F),
                                             F.coords.p, F.row_ptr.p, F.cols.p, h.L[m].vals.p);
   HOT_LAUNCH("k_rap");
@@ -646,61 +695,47 @@ void sgs_sweep(Scene &s, Topo &t, Vals<T> &V, bool forward) {
     int c = forward ? k : 26 - k;
     int nr = t.color_off[c + 1] - t.color_off[c];
     if (nr == 0) continue;
-    k_sgs_color<T><<<(unsigned)((nr + WPB - 1) / WPB), NT, 0, s.st>>>(t.color_list.p + t.color_off[c], nr,
-                                                                       t.row_ptr.p, t.cols.p, V.vals.p, V.dinv.p,
-                                                                       V.b.p, V.u.p);
+    ProfScope prof_(s, "sgs");
+    k_sgs_color<T><<<(unsigned)((nr + WPB * RPW - 1) / (WPB * RPW)), NT, 0, s.st>>>(
+        t.color_list.p + t.color_off[c], nr, t.row_ptr.p, t.cols.p, V.vals.p, V.dinv.p, V.b.p, V.u.p);
     HOT_LAUNCH("k_sgs_color");
   }
 }
 
 template <class T>
-int coarse_solve(Scene &s, Hier<T> &h, int m, int forced) {
+void coarse_solve(Scene &s, Hier<T> &h, int m) {
   Topo &t = s.topo[m];
   Vals<T> &V = h.L[m];
-  const int64_t n = t.n;
-  h.x.ensure(3 * n + 3);
-  h.r.ensure(3 * n + 3);
-  h.z.ensure(3 * n + 3);
-  h.p.ensure(3 * n + 3);
-  h.Ap.ensure(3 * n + 3);
-  h.bar.ensure(2);
-  h.info.ensure(2);
-  int G = (int)((n + WPB * 2 - 1) / (WPB * 2));
+  int64_t nn = t.n;
+  int G = (int)((nn + WPB * RPW - 1) / (WPB * RPW));
   int maxb = coop_blocks<T>();
   if (G > maxb) G = maxb;
   if (G < 1) G = 1;
-  h.part.ensure(2 * (size_t)G);
   HOT_CUDA(cudaMemsetAsync(h.bar.p, 0, 2 * sizeof(unsigned), s.st));
-  HOT_CUDA(cudaMemsetAsync(h.info.p, 0, 2 * sizeof(int), s.st));
-  int max_iter = s.opts.max_coarse_cg > 0 ? s.opts.max_coarse_cg : (int)(3 * n);
+  int max_iter = s.opts.max_coarse_cg > 0 ? s.opts.max_coarse_cg : (int)(3 * nn);
   double tau = s.opts.eps;
-  int64_t nn = n;
-  const int *rp = t.row_ptr.p;
-  const int *cl = t.cols.p;
-  const T *vv = V.vals.p;
-  const T *dg = V.diag.p;
-  const T *bb = V.b.p;
-  T *xx = h.x.p, *rr = h.r.p, *zz = h.z.p, *pp = h.p.p, *ap = h.Ap.p;
-  double *pt = h.part.p;
-  unsigned *br = h.bar.p;
-  int *inf = h.info.p;
-  int *er = s.errflag.p;
-  void *args[] = {&nn, &rp, &cl, &vv, &dg, &bb, &xx, &rr, &zz, &pp, &ap, &pt, &br, &inf, &er, &tau, &max_iter, &forced};
-  HOT_CUDA(cudaLaunchCooperativeKernel((void *)k_coarse_pcg<T>, dim3(G), dim3(NT), args, 0, s.st));
-  int its = 0;
-  HOT_CUDA(cudaMemcpyAsync(&its, h.info.p, sizeof(int), cudaMemcpyDeviceToHost, s.st));
-  HOT_CUDA(cudaMemcpyAsync(V.u.p, h.x.p, sizeof(T) * 3 * n, cudaMemcpyDeviceToDevice, s.st));
-  HOT_CUDA(cudaStreamSynchronize(s.st));
-  return its;
+  int cap = (int)h.cg_log.cap;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(NT);
+  cfg.stream = s.st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ProfScope prof_(s, "coarse_pcg");
+  HOT_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_pcg<T>, nn, (const int *)t.row_ptr.p, (const int *)t.cols.p,
+                              (const T *)V.vals.p, (const T *)V.diag.p, (const T *)V.b.p, V.u.p, h.r.p, h.z.p,
+                              h.p.p, h.Ap.p, h.part.p, h.bar.p, h.cg_log.p, h.cg_log.p + (cap - 1), cap - 1,
+                              s.errflag.p, tau, max_iter));
+  note_launch("k_coarse_pcg");
 }
-}  // namespace
 
-// Alg. 2: returns the coarsest PCG iteration count
 template <class T>
-int vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, int forced_cg) {
+void vcycle_launches(Scene &s, Hier<T> &h, const double *b_in, double *u_out) {
   const int M = s.nlev;
   Topo &t0 = s.topo[0];
-  if (t0.n == 0) return 0;
   k_load_rhs<T><<<(unsigned)((3 * t0.n + NT - 1) / NT), NT, 0, s.st>>>(t0.n, b_in, s.fixed.p, h.L[0].b.p);
   HOT_LAUNCH("k_load_rhs");
   for (int m = 0; m < M - 1; ++m) {
@@ -709,15 +744,18 @@ int vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, int forced_c
     HOT_CUDA(cudaMemsetAsync(V.u.p, 0, sizeof(T) * 3 * t.n, s.st));
     sgs_sweep<T>(s, t, V, true);
     sgs_sweep<T>(s, t, V, false);
-    k_residual<T><<<(unsigned)((t.n + WPB - 1) / WPB), NT, 0, s.st>>>(t.n, t.row_ptr.p, t.cols.p, V.vals.p, V.b.p,
-                                                                       V.u.p, V.r.p);
-    HOT_LAUNCH("k_residual");
+    {
+      ProfScope prof_(s, "residual");
+      k_residual<T><<<(unsigned)((t.n + WPB * RPW - 1) / (WPB * RPW)), NT, 0, s.st>>>(
+          t.n, t.row_ptr.p, t.cols.p, V.vals.p, V.b.p, V.u.p, V.r.p);
+      HOT_LAUNCH("k_residual");
+    }
     Topo &c = s.topo[m + 1];
     k_restrict<T><<<(unsigned)((c.n + NT - 1) / NT), NT, 0, s.st>>>(c.n, c.coords.p, t.map.p, dims_of(t), V.r.p,
                                                                      h.L[m + 1].b.p);
     HOT_LAUNCH("k_restrict");
   }
-  int its = coarse_solve<T>(s, h, M - 1, forced_cg);
+  coarse_solve<T>(s, h, M - 1);
   for (int m = M - 2; m >= 0; --m) {
     Topo &t = s.topo[m];
     Topo &c = s.topo[m + 1];
@@ -730,14 +768,100 @@ int vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, int forced_c
   }
   k_store_out<T><<<(unsigned)((3 * t0.n + NT - 1) / NT), NT, 0, s.st>>>(t0.n, h.L[0].u.p, s.fixed.p, u_out);
   HOT_LAUNCH("k_store_out");
-  return its;
+}
+}  // namespace
+
+// buffers the V-cycle touches, sized before any launch (and before capture)
+template <class T>
+void vcycle_prepare(Scene &s, Hier<T> &h) {
+  const int64_t n = s.topo[s.nlev - 1].n;
+  h.r.ensure(3 * n + 3);
+  h.z.ensure(3 * n + 3);
+  h.p.ensure(3 * n + 3);
+  h.Ap.ensure(3 * n + 3);
+  h.bar.ensure(2);
+  h.cg_log.ensure(4097, 1.0);
+  h.part.ensure(2 * (size_t)coop_blocks<T>() + 2);
+}
+
+// Alg. 2 on b_in -> u_out.  The coarsest PCG appends its iteration count to
+// the device log h.cg_log (read back with read_cg_log).  When the scene's
+// stream allows it, the launch sequence (fixed for a hierarchy) is captured
+// once into a CUDA graph and replayed.
+template <class T>
+void vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, bool use_graph) {
+  if (s.topo[0].n == 0) return;
+  vcycle_prepare<T>(s, h);
+  ProfScope prof_(s, "vcycle");
+  if (use_graph && s.graphs_ok && !(s.opts.flags & 1) && (!s.prof || s.prof_only == "vcycle")) {
+    if (s.vgraph && (s.vgraph_b != b_in || s.vgraph_u != u_out)) {
+      cudaGraphExecDestroy(s.vgraph);
+      s.vgraph = nullptr;
+    }
+    if (!s.vgraph) {
+      cudaGraph_t g = nullptr;
+      bool ok = cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        try {
+          vcycle_launches<T>(s, h, b_in, u_out);
+        } catch (const Error &) {
+          ok = false;
+        }
+        cudaError_t e = cudaStreamEndCapture(s.st, &g);
+        ok = ok && e == cudaSuccess && g != nullptr;
+        if (ok) ok = cudaGraphInstantiate(&s.vgraph, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+      }
+      cudaGetLastError();
+      if (!ok) {
+        s.vgraph = nullptr;
+        s.graphs_ok = false;   // run eagerly from now on
+      } else {
+        s.vgraph_b = b_in;
+        s.vgraph_u = u_out;
+      }
+    }
+    if (s.vgraph) {
+      HOT_CUDA(cudaGraphLaunch(s.vgraph, s.st));
+      note_launch("vcycle_graph");
+      ++s.graph_launches;
+      return;
+    }
+  }
+  vcycle_launches<T>(s, h, b_in, u_out);
+}
+
+template <class T>
+void reset_cg_log(Scene &s, Hier<T> &h) {
+  h.cg_log.ensure(4097, 1.0);
+  HOT_CUDA(cudaMemsetAsync(h.cg_log.p + (h.cg_log.cap - 1), 0, sizeof(int), s.st));
+}
+
+template <class T>
+std::vector<int> read_cg_log(Scene &s, Hier<T> &h) {
+  int cap = (int)h.cg_log.cap;
+  int cnt = 0;
+  HOT_CUDA(cudaMemcpyAsync(&cnt, h.cg_log.p + (cap - 1), sizeof(int), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  int k = cnt < cap - 1 ? cnt : cap - 1;
+  std::vector<int> out(k);
+  if (k > 0) {
+    HOT_CUDA(cudaMemcpyAsync(out.data(), h.cg_log.p, sizeof(int) * k, cudaMemcpyDeviceToHost, s.st));
+    HOT_CUDA(cudaStreamSynchronize(s.st));
+  }
+  out.resize(cnt, -1);   // entries beyond the log capacity are unknown
+  return out;
 }
 
 template void rap<double>(Scene &, Hier<double> &, int);
 template void rap<float>(Scene &, Hier<float> &, int);
 template void finalize_values<double>(Scene &, Hier<double> &, int);
 template void finalize_values<float>(Scene &, Hier<float> &, int);
-template int vcycle<double>(Scene &, Hier<double> &, const double *, double *, int);
-template int vcycle<float>(Scene &, Hier<float> &, const double *, double *, int);
+template void vcycle<double>(Scene &, Hier<double> &, const double *, double *, bool);
+template void vcycle<float>(Scene &, Hier<float> &, const double *, double *, bool);
+template void reset_cg_log<double>(Scene &, Hier<double> &);
+template void reset_cg_log<float>(Scene &, Hier<float> &);
+template std::vector<int> read_cg_log<double>(Scene &, Hier<double> &);
+template std::vector<int> read_cg_log<float>(Scene &, Hier<float> &);
 
 }  // namespace hot

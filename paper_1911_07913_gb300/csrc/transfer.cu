@@ -476,6 +476,7 @@ void p2g_transfer(Scene &s) {
   HOT_CUDA(cudaMemsetAsync(s.mv.p, 0, sizeof(double) * 3 * n, s.st));
   HOT_CUDA(cudaMemsetAsync(s.mxi.p, 0, sizeof(double) * n, s.st));
   if (s.n_blocks > 0) {
+    ProfScope prof_(s, "p2g");
     k_p2g<<<(unsigned)s.n_blocks, NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, s.blk_first.p, s.blk_end.p,
                                                  s.blk_key.p, g, s.topo[0].map.p, s.m.p, s.mv.p, s.mxi.p);
     HOT_LAUNCH("k_p2g");
@@ -504,6 +505,7 @@ double max_particle_speed(Scene &s) {
 void g2p_transfer(Scene &s, const double *vnew) {
   GeoArgs g = geo_args(s);
   if (s.np == 0) return;
+  ProfScope prof_(s, "g2p");
   k_g2p<<<(unsigned)((s.np + NT - 1) / NT), NT, 0, s.st>>>(s.pd.p, s.np, g, s.topo[0].map.p, vnew, s.dt);
   HOT_LAUNCH("k_g2p");
 }

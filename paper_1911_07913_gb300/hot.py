@@ -27,7 +27,8 @@ EXPORTED = ["mpm_set_allocator", "mpm_create_scene", "mpm_destroy_scene", "mpm_l
             "mpm_set_options", "mpm_p2g", "mpm_build_hierarchy", "mpm_solve_step", "mpm_g2p",
             "mpm_step", "mpm_get_state", "mpm_set_state", "mpm_get_grid", "mpm_eval_energy",
             "mpm_eval_gradient", "mpm_get_hessian", "mpm_apply_vcycle", "mpm_get_trace",
-            "mpm_scene_footprint", "mpm_step_batch"]
+            "mpm_scene_footprint", "mpm_step_batch", "mpm_profile", "mpm_profile_read",
+            "mpm_kernel_launch_count"]
 
 
 class mpm_material(C.Structure):
@@ -58,14 +59,16 @@ class mpm_solver_opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("cn_mode", C.c_int32), ("lbfgs_m", C.c_int32),
                 ("levels", C.c_int32), ("precision", C.c_int32), ("max_iters", C.c_int32),
                 ("max_ls", C.c_int32), ("max_coarse_cg", C.c_int32), ("record_trace", C.c_int32),
-                ("dt", C.c_double), ("fps", C.c_double), ("cfl", C.c_double)]
+                ("dt", C.c_double), ("fps", C.c_double), ("cfl", C.c_double), ("flags", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class mpm_step_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("ls_trials", C.c_int32), ("coarse_cg_iters", C.c_int32),
                 ("vcycles", C.c_int32), ("final_norm", C.c_double), ("energy", C.c_double),
                 ("dt_used", C.c_double), ("n_particles", C.c_int64), ("n_nodes", C.c_int64 * 8),
-                ("nnz_blocks", C.c_int64 * 8), ("n_levels", C.c_int32), ("status", C.c_int32)]
+                ("nnz_blocks", C.c_int64 * 8), ("n_levels", C.c_int32), ("status", C.c_int32),
+                ("graph_vcycles", C.c_int32), ("reserved", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -120,6 +123,11 @@ def load(install_torch_allocator: bool = True):
     lib.mpm_scene_footprint.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
     lib.mpm_step_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(mpm_step_stats)]
     lib.mpm_set_allocator.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.mpm_profile.argtypes = [C.c_void_p, C.c_int32, C.c_char_p]
+    lib.mpm_profile_read.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p,
+                                     C.c_void_p]
+    lib.mpm_kernel_launch_count.restype = C.c_int64
+    lib.mpm_kernel_launch_count.argtypes = []
     _lib = lib
     if install_torch_allocator:
         _install_torch_allocator(lib)
@@ -165,7 +173,7 @@ def opts_struct(o: _scenes.SolverOptions) -> mpm_solver_opts:
     return mpm_solver_opts(eps=o.eps, cn_mode=o.cn_mode, lbfgs_m=o.lbfgs_m, levels=o.levels,
                            precision=o.precision, max_iters=o.max_iters, max_ls=o.max_ls,
                            max_coarse_cg=o.max_coarse_cg, record_trace=1, dt=o.dt, fps=o.fps,
-                           cfl=o.cfl)
+                           cfl=o.cfl, flags=getattr(o, "flags", 0))
 
 
 def stats_dict(s: mpm_step_stats) -> dict:
@@ -174,7 +182,7 @@ def stats_dict(s: mpm_step_stats) -> dict:
             "vcycles": s.vcycles, "final_norm": s.final_norm, "energy": s.energy, "dt": s.dt_used,
             "n_particles": s.n_particles, "n_nodes": list(s.n_nodes[:nl]),
             "nnz_blocks": list(s.nnz_blocks[:nl]), "n_levels": nl, "status": s.status,
-            "status_name": STATUS.get(s.status, str(s.status))}
+            "status_name": STATUS.get(s.status, str(s.status)), "graph_vcycles": s.graph_vcycles}
 
 
 class HotScene:
@@ -348,10 +356,30 @@ class HotScene:
                 "skipped": sk[:k].tolist(), "fallback": fb[:k].tolist(),
                 "cg_counts": cg[:nv.value].tolist()}
 
+    def profile(self, enable: bool = True, only: Optional[str] = None):
+        self._check(self.lib.mpm_profile(self.h, 1 if enable else 0, only.encode() if only else None))
+
+    def profile_read(self) -> dict:
+        cap = 64
+        cnt = C.c_int32()
+        names = C.create_string_buffer(32 * cap)
+        ms = np.zeros(cap)
+        nl = np.zeros(cap, np.int64)
+        self._check(self.lib.mpm_profile_read(self.h, cap, C.byref(cnt), names, _ptr(ms), _ptr(nl)))
+        out = {}
+        for k in range(min(cnt.value, cap)):
+            nm = names.raw[32 * k:32 * (k + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = {"ms": float(ms[k]), "launches": int(nl[k])}
+        return out
+
     def footprint(self) -> int:
         b = C.c_int64()
         self._check(self.lib.mpm_scene_footprint(self.h, C.byref(b)))
         return b.value
+
+
+def kernel_launch_count() -> int:
+    return int(load().mpm_kernel_launch_count())
 
 
 def step_batch(scene_list, check=True):

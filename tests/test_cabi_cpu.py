@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "hot_mpm.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:mpm_status|const char \*)\s*(mpm_\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:mpm_status|const char \*|int64_t)\s*(mpm_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -39,8 +39,8 @@ def test_struct_sizes_match_header(lib_path):
     # sizes follow from the C layout rules on LP64 (x86-64 and aarch64 alike)
     assert ctypes.sizeof(hot.mpm_material) == 40
     assert ctypes.sizeof(hot.mpm_bc) == 8 + 12 * 8 + 8
-    assert ctypes.sizeof(hot.mpm_solver_opts) == 8 + 8 * 4 + 3 * 8
-    assert ctypes.sizeof(hot.mpm_step_stats) == 16 + 24 + 8 + 128 + 8
+    assert ctypes.sizeof(hot.mpm_solver_opts) == 8 + 8 * 4 + 3 * 8 + 8
+    assert ctypes.sizeof(hot.mpm_step_stats) == 16 + 24 + 8 + 128 + 8 + 8
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
