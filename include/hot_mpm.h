@@ -232,6 +232,34 @@ mpm_status mpm_scene_footprint(mpm_scene_t s, int64_t *bytes);
  * stats may be NULL, else n entries. */
 mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats);
 
+/* Elastic energy sum_p V_p psi(F_p) of a particle set, computed without any
+ * device allocation.  The paper has no counterpart: this serves callers that
+ * cannot allocate at the point of the call -- code running while a stream is
+ * captured into a CUDA graph (cudaMalloc would break or be refused by the
+ * capture), real-time loops that cannot afford the device synchronisation
+ * cudaMalloc/cudaFree imply, and hosts with a fixed, pre-reserved memory
+ * budget.  Every other entry point allocates through the allocator hook.
+ *
+ * F (n x 9 row-major), vol (n) and material_id (n, may be NULL = material 0;
+ * an id outside [0, n_materials) makes the result NaN) are device pointers; materials is a host array of 1..16 entries (models 0
+ * and 1 as in mpm_material).  energy receives the sum: a device pointer when
+ * energy_on_device is 1 (the call then returns without synchronising),
+ * otherwise a host pointer (the call synchronises the stream).
+ *
+ * Scratch: a fixed 512 KiB array in the library's device memory, held on
+ * every GPU that loads the library until the process exits.  Hence the
+ * limit n_particles <= 134,217,728 (2048 particles per partial sum); larger
+ * sets are rejected with MPM_ERR_INVALID_ARG.  The first call on a device
+ * looks the array's address up (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array: calls whose work overlaps on the GPU (different streams, or
+ * other threads) race and must be serialised by the caller.  Errors:
+ * INVALID_ARG, CUDA; message in mpm_last_error(NULL). */
+mpm_status mpm_particle_energy_noalloc(const double *F, const double *vol, const int32_t *material_id,
+                                       const mpm_material *materials, int32_t n_materials,
+                                       int64_t n_particles, double *energy, int32_t energy_on_device,
+                                       void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,8 @@ static std::atomic<long long> g_launches{0};
 
 void fail(mpm_status code, const std::string &msg) { throw Error{code, msg}; }
 
+void set_thread_error(const std::string &msg) { g_last_error = msg; }
+
 void note_launch(const char *what) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   check_cuda(cudaGetLastError(), what);

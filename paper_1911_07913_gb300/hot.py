@@ -28,7 +28,7 @@ EXPORTED = ["mpm_set_allocator", "mpm_create_scene", "mpm_destroy_scene", "mpm_l
             "mpm_step", "mpm_get_state", "mpm_set_state", "mpm_get_grid", "mpm_eval_energy",
             "mpm_eval_gradient", "mpm_get_hessian", "mpm_apply_vcycle", "mpm_get_trace",
             "mpm_scene_footprint", "mpm_step_batch", "mpm_profile", "mpm_profile_read",
-            "mpm_kernel_launch_count"]
+            "mpm_kernel_launch_count", "mpm_particle_energy_noalloc"]
 
 
 class mpm_material(C.Structure):
@@ -128,6 +128,8 @@ def load(install_torch_allocator: bool = True):
                                      C.c_void_p]
     lib.mpm_kernel_launch_count.restype = C.c_int64
     lib.mpm_kernel_launch_count.argtypes = []
+    lib.mpm_particle_energy_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(mpm_material),
+                                                C.c_int32, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p]
     _lib = lib
     if install_torch_allocator:
         _install_torch_allocator(lib)
@@ -376,6 +378,31 @@ class HotScene:
         b = C.c_int64()
         self._check(self.lib.mpm_scene_footprint(self.h, C.byref(b)))
         return b.value
+
+
+def particle_energy_noalloc(F_dev: int, vol_dev: int, mat_dev: int, materials, n: int,
+                            out_dev: Optional[int] = None, stream: int = 0) -> Optional[float]:
+    """Elastic energy of n particles from device arrays (F n x 9, vol n,
+    material ids n) without any device allocation: for callers that cannot
+    allocate (during graph capture, in allocation-free loops).  Returns the
+    value (host result) or None when out_dev (a device double*) is given."""
+    lib = load()
+    mats = (mpm_material * len(materials))(*[
+        mpm_material(m.E, m.nu, m.rho, m.yield_stress, m.model, m.plasticity) for m in materials])
+    if out_dev is None:
+        e = C.c_double()
+        code = lib.mpm_particle_energy_noalloc(C.c_void_p(F_dev), C.c_void_p(vol_dev), C.c_void_p(mat_dev),
+                                               mats, len(materials), n, C.cast(C.byref(e), C.c_void_p), 0,
+                                               C.c_void_p(stream) if stream else None)
+        if code != OK:
+            raise HotError(code, lib.mpm_last_error(None).decode())
+        return e.value
+    code = lib.mpm_particle_energy_noalloc(C.c_void_p(F_dev), C.c_void_p(vol_dev), C.c_void_p(mat_dev), mats,
+                                           len(materials), n, C.c_void_p(out_dev), 1,
+                                           C.c_void_p(stream) if stream else None)
+    if code != OK:
+        raise HotError(code, lib.mpm_last_error(None).decode())
+    return None
 
 
 def kernel_launch_count() -> int:
