@@ -109,7 +109,8 @@ typedef struct {
   double dt;             /* > 0: fixed step; else min(1/fps, cfl dx / v_max) */
   double fps;
   double cfl;
-  int32_t flags;         /* bit 0: run the V-cycle eagerly instead of as a CUDA graph */
+  int32_t flags;         /* bit 0: run the V-cycle eagerly instead of as a CUDA graph;
+                            bit 1: coarsest solve by the cooperative kernel, not the cluster one */
   int32_t reserved;
 } mpm_solver_opts;
 

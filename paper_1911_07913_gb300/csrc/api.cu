@@ -102,7 +102,8 @@ size_t Scene::bytes() const {
              blk_first.bytes() + blk_end.bytes() + blk_key.bytes() + flags.bytes() + flag_scan.bytes() + m.bytes() +
              v.bytes() + xi.bytes() + fixed.bytes() + mv.bytes() + mxi.bytes() + dv.bytes() + g.bytes() +
              pdir.bytes() + q.bytes() + g_new.bytes() + dv_new.bytes() + vtmp.bytes() + hist_s.bytes() +
-             hist_y.bytes() + Lv.bytes() + Lp.bytes() + Le.bytes() + dv_e.bytes() + g_e.bytes() + part.bytes() +
+             hist_y.bytes() + Lv.bytes() + Lp.bytes() + Le.bytes() + dv_e.bytes() + g_e.bytes() + gscr.bytes() +
+             part.bytes() +
              scal.bytes() + errflag.bytes() + scan.block_sums.bytes() + scan.total.bytes() + hd.bytes() + hf.bytes();
   for (auto &t : topo) b += t.bytes();
   return b;
@@ -110,7 +111,7 @@ size_t Scene::bytes() const {
 
 void Scene::release() {
   for (auto *b : {&pd, &pd_alt, &m, &v, &xi, &mv, &mxi, &dv, &g, &pdir, &q, &g_new, &dv_new, &vtmp, &hist_s,
-                  &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e})
+                  &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e, &gscr})
     b->release();
   for (auto *b : {&pmat, &pmat_alt, &pid, &pid_alt, &slot, &perm, &tmp, &cell_count, &cell_start, &cell_first,
                   &cell_n, &cell_key, &blk_first, &blk_end, &blk_key, &flags, &flag_scan, &errflag})
@@ -177,6 +178,7 @@ void do_p2g(Scene &s) {
 template <class T>
 void build_hier(Scene &s, Hier<T> &h) {
   const int64_t n = s.nn();
+  h.cl_level = -1;   // re-plan the coarsest solve for the new hierarchy
   s.Lv.ensure(9 * (size_t)s.np + 9);
   velocity_gradient(s, s.v.p, nullptr, s.Lv.p);      // F at dv = 0
   build_pattern0(s);

@@ -122,63 +122,70 @@ __global__ void k_energy(const double *__restrict__ pd, const int *__restrict__ 
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// gradient scatter: dt V_p P(F_p) F^n_p^T grad w_ip, one CTA per 4^3-cell block
-constexpr int NB6 = 216;
-__global__ void __launch_bounds__(NT) k_grad_scatter(const double *__restrict__ pd, const int *__restrict__ pmat,
-                                                     const MatParams *__restrict__ mt, int64_t np,
-                                                     const double *__restrict__ Lv, double dt,
-                                                     const int *__restrict__ blk_first, const int *__restrict__ blk_end,
-                                                     const int *__restrict__ blk_key, G g, const int *__restrict__ map,
-                                                     double *__restrict__ gout) {
-  __shared__ double acc[NB6 * 3];
-  for (int i = threadIdx.x; i < NB6 * 3; i += NT) acc[i] = 0.0;
-  __syncthreads();
-  const int key = blk_key[blockIdx.x];
-  const int o0 = (key % g.nb[0]) * 4, o1 = ((key / g.nb[0]) % g.nb[1]) * 4, o2 = (key / (g.nb[0] * g.nb[1])) * 4;
-  const int pe = blk_end[blockIdx.x];
-  for (int p = blk_first[blockIdx.x] + threadIdx.x; p < pe; p += NT) {
-    int b[3];
-    double fx[3], w[3][3], dw[3][3];
-    stencil(pd, np, p, g, b, fx, w, dw);
-    double F[9], P[9];
-    deformed(pd, np, p, Lv, nullptr, 0.0, dt, F);
-    const MatParams mp = mt[pmat[p]];
-    piola<double>(F, mp.mu, mp.lam, mp.model, P);
-    const double sc = dt * pd[PF_VOL * np + p];
-    double K[9];  // sc * P F^n^T
+// Two-phase gradient.  Phase 1, one thread per particle: K_p = dt V_p P(F_p)
+// F^n_p^T and the particle's per-axis weights w, dw (3 axes x 3 offsets) into
+// scratch (27 doubles per particle, SoA).  Phase 2, one warp per occupied
+// cell: lane k < 27 owns stencil node k of the cell and sums K_p grad w_kp
+// over the cell's particles in registers, then adds to the grid once.  No
+// shared-memory atomics, full warps in both phases.
+constexpr int GS_K = 0, GS_W = 9, GS_D = 18, GS_N = 27;
+__global__ void k_grad_particles(const double *__restrict__ pd, const int *__restrict__ pmat,
+                                 const MatParams *__restrict__ mt, int64_t np, const double *__restrict__ Lv,
+                                 double dt, G g, double *__restrict__ scr) {
+  int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (p >= np) return;
+  int b[3];
+  double fx[3], w[3][3], dw[3][3];
+  stencil(pd, np, p, g, b, fx, w, dw);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        K[3 * a + c] = sc * (P[3 * a] * pd[(PF_F + 3 * c) * np + p] + P[3 * a + 1] * pd[(PF_F + 3 * c + 1) * np + p] +
-                             P[3 * a + 2] * pd[(PF_F + 3 * c + 2) * np + p]);
-    const int l0 = b[0] - o0, l1 = b[1] - o1, l2 = b[2] - o2;
+    for (int k = 0; k < 3; ++k) {
+      scr[(GS_W + 3 * a + k) * np + p] = w[a][k];
+      scr[(GS_D + 3 * a + k) * np + p] = dw[a][k];
+    }
+  double F[9], P[9];
+  deformed(pd, np, p, Lv, nullptr, 0.0, dt, F);
+  const MatParams mp = mt[pmat[p]];
+  piola<double>(F, mp.mu, mp.lam, mp.model, P);
+  const double sc = dt * pd[PF_VOL * np + p];
 #pragma unroll
-    for (int kz = 0; kz < 3; ++kz)
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-          double gw[3] = {dw[0][kx] * w[1][ky] * w[2][kz], w[0][kx] * dw[1][ky] * w[2][kz],
-                          w[0][kx] * w[1][ky] * dw[2][kz]};
-          double *a = acc + 3 * (((l2 + kz) * 6 + (l1 + ky)) * 6 + (l0 + kx));
-          atomicAdd(a, K[0] * gw[0] + K[1] * gw[1] + K[2] * gw[2]);
-          atomicAdd(a + 1, K[3] * gw[0] + K[4] * gw[1] + K[5] * gw[2]);
-          atomicAdd(a + 2, K[6] * gw[0] + K[7] * gw[1] + K[8] * gw[2]);
-        }
+    for (int c = 0; c < 3; ++c)
+      scr[(GS_K + 3 * a + c) * np + p] =
+          sc * (P[3 * a] * pd[(PF_F + 3 * c) * np + p] + P[3 * a + 1] * pd[(PF_F + 3 * c + 1) * np + p] +
+                P[3 * a + 2] * pd[(PF_F + 3 * c + 2) * np + p]);
+}
+
+__global__ void k_grad_cells(const double *__restrict__ scr, int64_t np, const int *__restrict__ cell_first,
+                             const int *__restrict__ cell_n, const int *__restrict__ cell_key, int64_t ncell, G g,
+                             const int *__restrict__ map, double *__restrict__ gout) {
+  const int64_t c = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= ncell || lane >= 27) return;
+  const int kx = lane % 3, ky = (lane / 3) % 3, kz = lane / 9;
+  const int first = cell_first[c], cnt = cell_n[c];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int q = 0; q < cnt; ++q) {
+    const int64_t p = first + q;
+    const double wx = scr[(GS_W + kx) * np + p], wy = scr[(GS_W + 3 + ky) * np + p], wz = scr[(GS_W + 6 + kz) * np + p];
+    const double g0 = scr[(GS_D + kx) * np + p] * wy * wz;
+    const double g1 = wx * scr[(GS_D + 3 + ky) * np + p] * wz;
+    const double g2 = wx * wy * scr[(GS_D + 6 + kz) * np + p];
+    a0 += scr[(GS_K + 0) * np + p] * g0 + scr[(GS_K + 1) * np + p] * g1 + scr[(GS_K + 2) * np + p] * g2;
+    a1 += scr[(GS_K + 3) * np + p] * g0 + scr[(GS_K + 4) * np + p] * g1 + scr[(GS_K + 5) * np + p] * g2;
+    a2 += scr[(GS_K + 6) * np + p] * g0 + scr[(GS_K + 7) * np + p] * g1 + scr[(GS_K + 8) * np + p] * g2;
   }
-  __syncthreads();
-  for (int li = threadIdx.x; li < NB6; li += NT) {
-    const double *a = acc + 3 * li;
-    if (a[0] == 0.0 && a[1] == 0.0 && a[2] == 0.0) continue;
-    int x = o0 + li % 6, y = o1 + (li / 6) % 6, z = o2 + li / 36;
-    if (x >= g.nd[0] || y >= g.nd[1] || z >= g.nd[2]) continue;
-    int idx = map[nlin(x, y, z, g.nd)];
-    if (idx < 0) continue;
-    atomicAdd(gout + 3 * idx, a[0]);
-    atomicAdd(gout + 3 * idx + 1, a[1]);
-    atomicAdd(gout + 3 * idx + 2, a[2]);
-  }
+  const unsigned key = (unsigned)cell_key[c];
+  const unsigned B = key >> 6, l = key & 63u;
+  const int x = (int)(B % g.nb[0]) * 4 + (l & 3) + kx;
+  const int y = (int)((B / g.nb[0]) % g.nb[1]) * 4 + ((l >> 2) & 3) + ky;
+  const int z = (int)(B / (g.nb[0] * g.nb[1])) * 4 + (l >> 4) + kz;
+  const int idx = map[nlin(x, y, z, g.nd)];
+  atomicAdd(gout + 3 * idx, a0);
+  atomicAdd(gout + 3 * idx + 1, a1);
+  atomicAdd(gout + 3 * idx + 2, a2);
 }
 
 // node terms m_i (dv_i - dt g), projection, and the two termination norms
@@ -400,12 +407,15 @@ double energy(Scene &s, const double *L1, const double *L2, double alpha, const 
 void gradient(Scene &s, const double *Lcur, const double *dvec, double *gout, double norms[2]) {
   const int64_t nn = s.nn();
   HOT_CUDA(cudaMemsetAsync(gout, 0, sizeof(double) * 3 * nn, s.st));
-  if (s.n_blocks > 0) {
+  if (s.n_cells > 0) {
+    s.gscr.ensure((size_t)GS_N * s.np, 1.0);
     ProfScope prof_(s, "grad_scatter");
-    k_grad_scatter<<<(unsigned)s.n_blocks, NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, Lcur, s.dt,
-                                                          s.blk_first.p, s.blk_end.p, s.blk_key.p, geo(s),
-                                                          s.topo[0].map.p, gout);
-    HOT_LAUNCH("k_grad_scatter");
+    k_grad_particles<<<(unsigned)((s.np + NT - 1) / NT), NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np,
+                                                                        Lcur, s.dt, geo(s), s.gscr.p);
+    HOT_LAUNCH("k_grad_particles");
+    k_grad_cells<<<(unsigned)((s.n_cells + NT / 32 - 1) / (NT / 32)), NT, 0, s.st>>>(
+        s.gscr.p, s.np, s.cell_first.p, s.cell_n.p, s.cell_key.p, s.n_cells, geo(s), s.topo[0].map.p, gout);
+    HOT_LAUNCH("k_grad_cells");
   }
   const int nb = s.nsm;
   s.part.ensure(4096);

@@ -72,6 +72,10 @@ struct Hier {
   DBuf<double> part;                   // PCG partial sums
   DBuf<unsigned int> bar;              // grid barrier words
   DBuf<int> cg_log;                    // PCG iteration counts; last entry = count
+  int cl_level = -1;                   // coarsest level planned for the cluster solver (-1: none)
+  int cl_bounds[9] = {0};
+  int cl_rows_max = 0, cl_nb_max = 0;
+  size_t cl_smem = 0;                  // 0: level does not fit one cluster
   void set_stream(cudaStream_t st) {
     for (auto &l : L) l.set_stream(st);
     A45.st = x.st = r.st = z.st = p.st = Ap.st = st;
@@ -157,6 +161,7 @@ struct Scene {
   DBuf<double> hist_s, hist_y; // MAX_HIST x 3n
   DBuf<double> Lv, Lp;         // 9 np: sum_i u_i grad w_ip^T for v^n+dv and for p
   DBuf<double> Le, dv_e, g_e;  // scratch of the evaluation entry points
+  DBuf<double> gscr;           // 27 np: per-particle K and weight tables of the gradient
   DBuf<double> part;           // partial sums
   DBuf<double> scal;           // device scalars
   DBuf<int> errflag;
@@ -197,7 +202,7 @@ struct Scene {
   void set_stream(cudaStream_t s) {
     st = s;
     for (auto *b : {&pd, &pd_alt, &m, &v, &xi, &mv, &mxi, &dv, &g, &pdir, &q, &g_new, &dv_new, &vtmp,
-                    &hist_s, &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e})
+                    &hist_s, &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e, &gscr})
       b->st = s;
     for (auto *b : {&pmat, &pmat_alt, &pid, &pid_alt, &slot, &perm, &tmp, &cell_count, &cell_start,
                     &cell_first, &cell_n, &cell_key, &blk_first, &blk_end, &blk_key, &flags, &flag_scan,

@@ -560,6 +560,123 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Coarsest level on one thread-block cluster: the level's rows are split
+// over CL CTAs by block count and kept in their shared memory; every CTA holds
+// the whole search direction p.  Partial dot products and each CTA's slice
+// of p are written into the other CTAs' shared memory (distributed shared
+// memory) and cluster.sync() -- a hardware barrier -- separates the phases.
+// Same Jacobi-PCG iteration and stopping rule as k_coarse_pcg.
+// ---------------------------------------------------------------------------
+constexpr int CL = 8;
+constexpr int CNT = 512;
+struct ClusterPlan {
+  int bounds[CL + 1];
+};
+
+template <class T>
+__global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__restrict__ row_ptr,
+                                                            const int *__restrict__ gcols,
+                                                            const T *__restrict__ gvals,
+                                                            const T *__restrict__ gdiag, const T *__restrict__ b,
+                                                            T *__restrict__ xout, ClusterPlan plan, int rows_max,
+                                                            int nb_max, double tau, int max_iter, int *log,
+                                                            int *log_idx, int log_cap) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ double sh[CNT];
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int rank = (int)cluster.block_rank();
+  double *redA = reinterpret_cast<double *>(sm);
+  double *redB = redA + CL;
+  T *pfull = reinterpret_cast<T *>(redB + CL);
+  T *x = pfull + 3 * R;
+  T *r = x + 3 * rows_max;
+  T *z = r + 3 * rows_max;
+  T *Ap = z + 3 * rows_max;
+  T *dg = Ap + 3 * rows_max;
+  T *vals = dg + 3 * rows_max;
+  int *rptr = reinterpret_cast<int *>(vals + 9 * (int64_t)nb_max);
+  int *cols = rptr + rows_max + 1;
+  const int r0 = plan.bounds[rank], r1 = plan.bounds[rank + 1], nr = r1 - r0;
+  const int g0 = row_ptr[r0], nbl = row_ptr[r1] - g0;
+  cluster.sync();   // every CTA of the cluster is running before any remote access
+  for (int k = threadIdx.x; k <= nr; k += CNT) rptr[k] = row_ptr[r0 + k] - g0;
+  for (int k = threadIdx.x; k < nbl; k += CNT) cols[k] = gcols[g0 + k];
+  for (int k = threadIdx.x; k < 9 * nbl; k += CNT) vals[k] = gvals[9 * (int64_t)g0 + k];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < 3 * nr; k += CNT) {
+    const T d = gdiag[3 * r0 + k], bk = b[3 * r0 + k];
+    dg[k] = d;
+    x[k] = T(0);
+    r[k] = bk;
+    const T zk = bk / d;
+    z[k] = zk;
+    for (int dst = 0; dst < CL; ++dst) cluster.map_shared_rank(pfull, dst)[3 * r0 + k] = zk;
+    acc += (double)bk * (double)zk;
+  }
+  double t = block_sum<CNT>(acc, sh);
+  if (threadIdx.x < CL) cluster.map_shared_rank(redA, threadIdx.x)[rank] = t;
+  cluster.sync();
+  double rz = 0.0;
+  for (int k = 0; k < CL; ++k) rz += redA[k];
+  const double bn = sqrt(fmax(rz, 0.0));
+  const double kk = fmax(fmin(0.5, sqrt(fmax(bn, tau))), sizeof(T) == 4 ? 1e-3 : 0.0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int it = 0;
+  while (true) {
+    if (sqrt(fmax(rz, 0.0)) <= kk * bn || it >= max_iter) break;
+    acc = 0.0;
+    for (int i = warp; i < nr; i += CNT / 32) {
+      T a3[3];
+      row_product<T>(i, true, lane, rptr, cols, vals, pfull, false, a3);
+      if (lane == 0) {
+        Ap[3 * i] = a3[0];
+        Ap[3 * i + 1] = a3[1];
+        Ap[3 * i + 2] = a3[2];
+        const T *pp = pfull + 3 * (r0 + i);
+        acc += (double)pp[0] * (double)a3[0] + (double)pp[1] * (double)a3[1] + (double)pp[2] * (double)a3[2];
+      }
+    }
+    t = block_sum<CNT>(acc, sh);
+    if (threadIdx.x < CL) cluster.map_shared_rank(redB, threadIdx.x)[rank] = t;
+    cluster.sync();
+    double pAp = 0.0;
+    for (int k = 0; k < CL; ++k) pAp += redB[k];
+    if (!(pAp > 0.0)) break;
+    const double alpha = rz / pAp;
+    acc = 0.0;
+    for (int k = threadIdx.x; k < 3 * nr; k += CNT) {
+      x[k] += (T)alpha * pfull[3 * r0 + k];
+      const T rk = r[k] - (T)alpha * Ap[k];
+      r[k] = rk;
+      const T zk = rk / dg[k];
+      z[k] = zk;
+      acc += (double)rk * (double)zk;
+    }
+    t = block_sum<CNT>(acc, sh);
+    if (threadIdx.x < CL) cluster.map_shared_rank(redA, threadIdx.x)[rank] = t;
+    cluster.sync();
+    double rz_new = 0.0;
+    for (int k = 0; k < CL; ++k) rz_new += redA[k];
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (int k = threadIdx.x; k < 3 * nr; k += CNT) {
+      const T pk = z[k] + (T)beta * pfull[3 * r0 + k];
+      for (int dst = 0; dst < CL; ++dst) cluster.map_shared_rank(pfull, dst)[3 * r0 + k] = pk;
+    }
+    cluster.sync();
+    ++it;
+  }
+  for (int k = threadIdx.x; k < 3 * nr; k += CNT) xout[3 * r0 + k] = x[k];
+  if (rank == 0 && threadIdx.x == 0) {
+    int k = *log_idx;
+    if (k < log_cap) log[k] = it;
+    *log_idx = k + 1;
+  }
+  cluster.sync();   // no CTA leaves while another may still address its shared memory
+}
+
 template <class T>
 int coop_blocks() {
   static int cached = -1;
@@ -702,19 +819,96 @@ void sgs_sweep(Scene &s, Topo &t, Vals<T> &V, bool forward) {
   }
 }
 
+// Partition of the coarsest level over one cluster, computed once per
+// hierarchy; cl_smem = 0 when the level does not fit (cooperative fallback).
+template <class T>
+void plan_cluster(Scene &s, Hier<T> &h, int m) {
+  Topo &t = s.topo[m];
+  h.cl_level = m;
+  h.cl_smem = 0;
+  const int R = (int)t.n;
+  if (R == 0) return;
+  std::vector<int> rp(R + 1);
+  HOT_CUDA(cudaMemcpyAsync(rp.data(), t.row_ptr.p, sizeof(int) * (R + 1), cudaMemcpyDeviceToHost, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  const int64_t B = rp[R];
+  int r = 0;
+  h.cl_bounds[0] = 0;
+  for (int c = 1; c < CL; ++c) {
+    const int64_t target = B * c / CL;
+    while (r < R && rp[r] < target) ++r;
+    h.cl_bounds[c] = r;
+  }
+  h.cl_bounds[CL] = R;
+  int rows_max = 0, nb_max = 0;
+  for (int c = 0; c < CL; ++c) {
+    rows_max = std::max(rows_max, h.cl_bounds[c + 1] - h.cl_bounds[c]);
+    nb_max = std::max(nb_max, rp[h.cl_bounds[c + 1]] - rp[h.cl_bounds[c]]);
+  }
+  size_t bytes = 2 * CL * sizeof(double) + sizeof(T) * (3 * (size_t)R + 5 * 3 * (size_t)rows_max + 9 * (size_t)nb_max) +
+                 sizeof(int) * ((size_t)rows_max + 1 + nb_max) + 64;
+  if (bytes > 200 * 1024) return;
+  HOT_CUDA(cudaFuncSetAttribute(k_coarse_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(CNT);
+  cfg.dynamicSmemBytes = bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_pcg_cluster<T>, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return;
+  }
+  h.cl_rows_max = rows_max;
+  h.cl_nb_max = nb_max;
+  h.cl_smem = bytes;
+}
+
 template <class T>
 void coarse_solve(Scene &s, Hier<T> &h, int m) {
   Topo &t = s.topo[m];
   Vals<T> &V = h.L[m];
   int64_t nn = t.n;
+  const int cap = (int)h.cg_log.cap;
+  // float32 coarse matrices of stiff scenes can lose definiteness to rounding,
+  // where CG stalls short of its tolerance: cap float32 runs at 100 iterations
+  const int max_iter = s.opts.max_coarse_cg > 0 ? s.opts.max_coarse_cg
+                                                : (int)(sizeof(T) == 4 ? std::min<int64_t>(3 * nn, 100) : 3 * nn);
+  if (h.cl_smem > 0 && !(s.opts.flags & 2)) {
+    ClusterPlan plan;
+    for (int c = 0; c <= CL; ++c) plan.bounds[c] = h.cl_bounds[c];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(CNT);
+    cfg.dynamicSmemBytes = h.cl_smem;
+    cfg.stream = s.st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ProfScope prof_(s, "coarse_pcg");
+    HOT_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_pcg_cluster<T>, (int)nn, (const int *)t.row_ptr.p,
+                                (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.diag.p, (const T *)V.b.p,
+                                V.u.p, plan, h.cl_rows_max, h.cl_nb_max, s.opts.eps, max_iter, h.cg_log.p,
+                                h.cg_log.p + (cap - 1), cap - 1));
+    note_launch("k_coarse_pcg_cluster");
+    return;
+  }
   int G = (int)((nn + WPB * RPW - 1) / (WPB * RPW));
   int maxb = coop_blocks<T>();
   if (G > maxb) G = maxb;
   if (G < 1) G = 1;
   HOT_CUDA(cudaMemsetAsync(h.bar.p, 0, 2 * sizeof(unsigned), s.st));
-  int max_iter = s.opts.max_coarse_cg > 0 ? s.opts.max_coarse_cg : (int)(3 * nn);
   double tau = s.opts.eps;
-  int cap = (int)h.cg_log.cap;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);
   cfg.blockDim = dim3(NT);
@@ -782,6 +976,7 @@ void vcycle_prepare(Scene &s, Hier<T> &h) {
   h.bar.ensure(2);
   h.cg_log.ensure(4097, 1.0);
   h.part.ensure(2 * (size_t)coop_blocks<T>() + 2);
+  if (h.cl_level != s.nlev - 1) plan_cluster<T>(s, h, s.nlev - 1);
 }
 
 // Alg. 2 on b_in -> u_out.  The coarsest PCG appends its iteration count to
