@@ -470,6 +470,7 @@ class Level:
     R: Optional[sp.csr_matrix]     # scalar restriction to the next level (n_next x n)
     colors: List[np.ndarray]       # node indices per color 0..26
     Dblk: np.ndarray               # (n,3,3) diagonal blocks
+    row_slices: Optional[dict] = None   # cache: color -> rows of H (no arithmetic)
 
 
 def node_colors(coords):
@@ -482,6 +483,7 @@ def node_colors(coords):
 
 
 def diag_blocks(H, n):
+    """The 3x3 diagonal blocks H_ii."""
     D = np.zeros((n, 3, 3))
     Hc = H.tocsr()
     for a in range(3):
@@ -527,8 +529,12 @@ def sgs(level: Level, u, b, forward=True):
         rows = level.colors[c]
         if rows.size == 0:
             continue
-        r3 = (3 * rows[:, None] + np.arange(3)[None, :]).ravel()
-        Hu = (H[r3] @ u.ravel()).reshape(-1, 3)
+        if level.row_slices is None:
+            level.row_slices = {}
+        if c not in level.row_slices:
+            r3 = (3 * rows[:, None] + np.arange(3)[None, :]).ravel()
+            level.row_slices[c] = H[r3]
+        Hu = (level.row_slices[c] @ u.ravel()).reshape(-1, 3)
         D = level.Dblk[rows]
         rhs = b[rows] - Hu + np.einsum("nab,nb->na", D, u[rows])
         u[rows] = np.linalg.solve(D, rhs[..., None])[..., 0]
