@@ -758,15 +758,56 @@ def step_dt(sc, opts):
     return min(1.0 / opts.fps, opts.cfl * sc.dx / vmax)
 
 
+def plasticity(F, mu, plastic, yield_stress):
+    """Lagged plastic projection of the deformation gradient, once per step
+    after the F update (the paper lags plasticity to keep the step a
+    minimisation; it prints no formulas, READING):
+      1 von Mises: principal Hencky strains e = ln s, deviatoric part
+        d = e - tr(e)/3; if 2 mu |d| > tau_Y, d is scaled onto the yield
+        surface 2 mu |d| = tau_Y (tr e, hence det F, unchanged);
+      2 snow: singular values clamped into [0.99, 1.001] (Table 2).
+    F = U diag(s) V^T with the inversion-safe SVD; other rows unchanged."""
+    out = F.copy()
+    vm = plastic == 1
+    if np.any(vm):
+        U, s, V = signed_svd(F[vm])
+        e = np.log(np.maximum(s, 1e-300))
+        dev = e - e.mean(axis=1, keepdims=True)
+        nd = np.sqrt(np.sum(dev * dev, axis=1))
+        ty = yield_stress[vm]
+        m = mu[vm]
+        yielding = 2.0 * m * nd > ty
+        scale = np.where(yielding, ty / np.maximum(2.0 * m * nd, 1e-300), 1.0)
+        e_new = e.mean(axis=1, keepdims=True) + dev * scale[:, None]
+        rebuilt = np.einsum("nij,nj,nkj->nik", U, np.exp(e_new), V)
+        idx = np.nonzero(vm)[0]
+        out[idx[yielding]] = rebuilt[yielding]
+    sn = plastic == 2
+    if np.any(sn):
+        U, s, V = signed_svd(F[sn])
+        s_new = np.clip(s, 0.99, 1.001)
+        changed = np.any(s_new != s, axis=1)
+        rebuilt = np.einsum("nij,nj,nkj->nik", U, s_new, V)
+        idx = np.nonzero(sn)[0]
+        out[idx[changed]] = rebuilt[changed]
+    return out
+
+
 def g2p(sc, grid: Grid, v_new, dt):
     """APIC G2P: v_p = sum_i w_ip v_i; C_p = 4/dx^2 sum_i w_ip v_i (x_i - x_p)^T;
-    F_p <- (I + dt sum_i v_i grad w_ip^T) F_p; x_p <- x_p + dt v_p."""
+    F_p <- (I + dt sum_i v_i grad w_ip^T) F_p, then the lagged plastic
+    projection; x_p <- x_p + dt v_p."""
     vi = v_new[grid.pidx]                                   # (N,27,3)
     vp = np.einsum("pk,pka->pa", grid.w, vi)
     rel = grid.pos[grid.pidx] - sc.x[:, None, :]
     Cp = (4.0 / grid.dx ** 2) * np.einsum("pk,pka,pkb->pab", grid.w, vi, rel)
     L = np.einsum("pka,pkb->pab", vi, grid.gw)
     F = (np.eye(3)[None] + dt * L) @ sc.F
+    plastic = np.array([m.plasticity for m in sc.materials])[sc.mat]
+    if np.any(plastic):
+        mu, _, _ = material_arrays(sc)
+        ty = np.array([m.yield_stress for m in sc.materials])[sc.mat]
+        F = plasticity(F, mu, plastic, ty)
     out = sc.copy()
     out.v = vp
     out.C = Cp

@@ -521,3 +521,45 @@ def test_stretched_box_converges_in_tens_of_iterations():
     tr = info["trace"]
     assert tr.status == "ok"
     assert 2 <= tr.iters <= 10 * gold["stretched_box_hot_iterations"]
+
+
+# ---------------------------------------------------------------- plasticity
+def test_von_mises_return_mapping():
+    rng = np.random.default_rng(21)
+    F = np.concatenate([rand_F(rng, 20, amp=0.25), rand_F(rng, 20, amp=0.003)])
+    F = F[np.linalg.det(F) > 0.3]
+    n = F.shape[0]
+    mu = np.full(n, 5e4)
+    ty = np.full(n, 2e3)
+    out = O.plasticity(F, mu, np.ones(n, int), ty)
+    # volume (det F) preserved; final state on or inside the yield surface
+    np.testing.assert_allclose(np.linalg.det(out), np.linalg.det(F), rtol=1e-12)
+    s = np.linalg.svd(out, compute_uv=False)
+    e = np.log(s)
+    dev = e - e.mean(1, keepdims=True)
+    tau = 2 * mu * np.sqrt((dev ** 2).sum(1))
+    assert np.all(tau <= ty * (1 + 1e-10))
+    s0 = np.linalg.svd(F, compute_uv=False)
+    e0 = np.log(s0)
+    tau0 = 2 * mu * np.sqrt(((e0 - e0.mean(1, keepdims=True)) ** 2).sum(1))
+    yielded = tau0 > ty
+    assert yielded.any() and (~yielded).any()
+    np.testing.assert_allclose(tau[yielded], ty[yielded], rtol=1e-10)
+    assert np.array_equal(out[~yielded], F[~yielded])
+    # rotation invariance
+    Q = rand_rot(rng, n)
+    np.testing.assert_allclose(O.plasticity(Q @ F, mu, np.ones(n, int), ty), Q @ out, atol=1e-12)
+
+
+def test_snow_clamp():
+    rng = np.random.default_rng(22)
+    F = rand_F(rng, 30, amp=0.05)
+    F = F[np.linalg.det(F) > 0]
+    n = F.shape[0]
+    out = O.plasticity(F, np.ones(n), np.full(n, 2), np.zeros(n))
+    s = np.linalg.svd(out, compute_uv=False)
+    assert s.min() >= 0.99 - 1e-14 and s.max() <= 1.001 + 1e-14
+    inside = np.eye(3)[None] * np.array([1.0005, 0.995, 1.0])[None, None, :]
+    assert np.array_equal(O.plasticity(inside, np.ones(1), np.full(1, 2), np.zeros(1)), inside)
+    Q = rand_rot(rng, n)
+    np.testing.assert_allclose(O.plasticity(Q @ F, np.ones(n), np.full(n, 2), np.zeros(n)), Q @ out, atol=1e-13)
