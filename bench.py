@@ -246,6 +246,109 @@ def run_e2e(g, sc, steps, stream, st):
             "ms_per_step": 1e3 * secs / steps}
 
 
+def run_batching(seed, steps, count=64):
+    """64 independent scenes (particle counts log-uniform 5k-200k, grids
+    64^3-128^3, E log-uniform 1e4-1e8, half von Mises, FP32 preconditioner)
+    stepped together: each scene on its own stream, driven by its own host
+    thread, so their kernels overlap on the GPU."""
+    import torch
+    from paper_1911_07913_gb300 import hot
+    scs = scenes.batch_scenes(seed=seed, count=count)
+    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500)
+    gs = [hot.HotScene(sc, opts) for sc in scs]
+    hot.step_batch(gs, check=False)       # warm-up: allocations, first hierarchy
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = []
+    for _ in range(steps):
+        st = hot.step_batch(gs, check=False)
+        iters.append(sum(x["iters"] for x in st))
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    n_total = sum(sc.n for sc in scs)
+    # the same scenes one after another, for comparison
+    t1 = time.perf_counter()
+    for g in gs:
+        g.step(check=False)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    for g in gs:
+        g.close()
+    return {"value": n_total * steps / secs, "unit": UNIT, "scenes": count, "particles": n_total,
+            "ms_per_batch_step": 1e3 * secs / steps, "sequential_value": n_total / seq,
+            "speedup_vs_sequential": (n_total * steps / secs) / (n_total / seq),
+            "lbfgs_iters_per_batch_step": iters,
+            "config": "64 boxes, N_p log-uniform 5k-200k, grids 64^3/96^3/128^3, FCR E log-uniform 1e4-1e8, "
+                      "half von Mises (yield 1e4 Pa), FP32 preconditioner, 3 levels, CN eps 1e-7, CFL dt"}
+
+
+def run_serving(seed, count=256, requests=512, workers=12, budget_gb=150.0, load=0.8):
+    """Resident scenes behind the continuous-batching server: a saturating
+    burst measures capacity, then a Poisson stream at `load` of that capacity
+    measures request latency (arrival -> result)."""
+    import torch
+    from paper_1911_07913_gb300 import hot
+    scs = scenes.serving_scenes(seed=seed, count=count)
+    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500)
+    gs = [hot.HotScene(sc, opts) for sc in scs]
+    srv = hot.StepServer(budget_bytes=int(budget_gb * (1 << 30)), n_workers=workers)
+    for i, g in enumerate(gs):           # first step of every scene: buffers become resident
+        srv.submit(g, i)
+    while srv.poll(wait=True) is not None:
+        pass
+    footprint = sum(g.footprint() for g in gs)
+    rng = np.random.default_rng(seed + 1)
+    # capacity: a burst of requests
+    pick = rng.integers(count, size=requests)
+    t0 = time.perf_counter()
+    for r, i in enumerate(pick):
+        srv.submit(gs[i], r)
+    done = 0
+    while srv.poll(wait=True) is not None:
+        done += 1
+    cap_s = time.perf_counter() - t0
+    cap_rate = requests / cap_s
+    cap_particles = sum(scs[i].n for i in pick) / cap_s
+    # Poisson arrivals at a fraction of capacity
+    rate = load * cap_rate
+    pick = rng.integers(count, size=requests)
+    gaps = rng.exponential(1.0 / rate, size=requests)
+    lat = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for r, i in enumerate(pick):
+        t_next += gaps[r]
+        while True:
+            now = time.perf_counter()
+            if now >= t_next:
+                break
+            out = srv.poll(wait=False)
+            if out is not None:
+                lat.append(out["latency_s"])
+            else:
+                time.sleep(min(5e-4, t_next - now))
+        srv.submit(gs[i], requests + r)
+    while True:
+        out = srv.poll(wait=True)
+        if out is None:
+            break
+        lat.append(out["latency_s"])
+    wall = time.perf_counter() - t0
+    info = srv.info()
+    srv.close()
+    for g in gs:
+        g.close()
+    lat = np.array(lat) * 1e3
+    return {"value": sum(scs[i].n for i in pick) / wall, "unit": UNIT, "scenes": count,
+            "resident_particles": sum(sc.n for sc in scs), "resident_footprint_gb": footprint / 2 ** 30,
+            "requests": requests, "workers": workers, "budget_gb": budget_gb,
+            "capacity_requests_per_s": cap_rate, "capacity_particle_steps_per_s": cap_particles,
+            "offered_load": load, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "peak_in_flight_gb": info["peak_in_flight_bytes"] / 2 ** 30,
+            "config": "resident scenes, N_p lognormal (median 50k, sigma 1, <= 1M), E log-uniform 1e4-1e9, FCR/NH, "
+                      "every third von Mises, FP32 preconditioner, 3 levels, CN eps 1e-7; Poisson arrivals"}
+
+
 def cpu_baseline_sample():
     """The oracle, as it stands, on a bounded sample of the same workload: the
     two-bar scene at the same dx, materials and boundary conditions, with bars
@@ -305,13 +408,17 @@ def main():
     ap.add_argument("--small", action="store_true", help="8k-particle cube (for profiling runs)")
     ap.add_argument("--workload", default="two_bars_600k", choices=["two_bars_600k", "two_bars_2m", "cube8k"])
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-scenes", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--profile-run", action="store_true",
                     help="profiling run under ncu: only the timed steps of one workload, warm-up allowed below 3")
     args = ap.parse_args()
     if args.small:
         args.workload = "cube8k"
     if args.profile_run:
-        args.no_mixed = args.no_e2e = args.no_cpu = True
+        args.no_mixed = args.no_e2e = args.no_cpu = args.no_batch = args.no_serve = True
     elif args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -352,6 +459,12 @@ def main():
                  "roofline": roofline_entry("vcycle", r2["prof"], r2["stats"], sc2.n, 1, peaks),
                  "kernel_ms": {k: round(v["ms"], 3) for k, v in r2["breakdown"].items()},
                  "clocks": r2["clocks"]}
+    batching = serving = None
+    if args.workload == "two_bars_600k" and args.precision == 0:
+        if not args.no_batch:
+            batching = run_batching(rank, max(2, args.steps // 2))
+        if not args.no_serve:
+            serving = run_serving(rank, count=args.serve_scenes, requests=args.serve_requests)
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline_sample()
@@ -365,7 +478,8 @@ def main():
             "iters": [s["iters"] for s in r["stats"]],
             "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "roofline": roof,
             "kernel_ms_one_step": {k: round(v["ms"], 3) for k, v in r["breakdown"].items()},
-            "clocks": r["clocks"], "mixed": mixed, "cpu_baseline": cpu}
+            "clocks": r["clocks"], "mixed": mixed, "batching": batching, "serving": serving,
+            "cpu_baseline": cpu}
     print(json.dumps(line))
 
 

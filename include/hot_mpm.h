@@ -57,7 +57,11 @@ typedef enum {
 } mpm_status;
 
 /* Material (Sec. 6.1, Table 2).  model 0: fixed corotated (Stomakhin et al.
- * 2012); 1: compressible Neo-Hookean.  plasticity is reserved (0). */
+ * 2012); 1: compressible Neo-Hookean.  plasticity, applied once per step
+ * after the F update (lagged, Sec. 2.2): 0 none; 1 von Mises, the
+ * deviatoric principal Hencky strain returned onto 2 mu |dev ln s| =
+ * yield_stress (yield_stress > 0 required); 2 snow-like clamp of the
+ * singular values of F into [0.99, 1.001] (Table 2). */
 typedef struct {
   double E, nu, rho, yield_stress;
   int32_t model;
@@ -232,6 +236,29 @@ mpm_status mpm_scene_footprint(mpm_scene_t s, int64_t *bytes);
  * the same stream run back to back; scenes on different streams overlap.
  * stats may be NULL, else n entries. */
 mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats);
+
+/* Continuous-batching step server (serving many resident scenes).  Requests
+ * (one implicit step of a scene each) queue in FIFO order and are admitted
+ * when a worker is free, the scene is not already being stepped, and the
+ * summed device footprint of the scenes in flight plus this scene's stays
+ * within budget_bytes (a lone request is always admitted).  Each worker
+ * thread steps its scene with mpm_step on the scene's own stream, so admitted
+ * requests overlap on the GPU.  Scenes stay resident between requests (their
+ * grids, hierarchy buffers and L-BFGS storage remain allocated); create them
+ * with cuda_stream = NULL so that each gets its own stream.
+ *   submit: MPM_ERR_ADMISSION if the scene alone exceeds the budget.
+ *   poll:   *request_id = -1 when nothing has finished (wait = 0) or nothing
+ *           is pending (wait = 1); latency = submit -> finish, queue = submit
+ *           -> start, seconds; step_status = the step's mpm_status.
+ *   destroy: waits for queued and running requests. */
+typedef struct mpm_server *mpm_server_t;
+mpm_status mpm_server_create(int64_t budget_bytes, int32_t n_workers, mpm_server_t *out);
+mpm_status mpm_server_submit(mpm_server_t server, mpm_scene_t scene, int64_t request_id);
+mpm_status mpm_server_poll(mpm_server_t server, int32_t wait, int64_t *request_id, mpm_step_stats *stats,
+                           double *latency_s, double *queue_s, int32_t *step_status);
+mpm_status mpm_server_info(mpm_server_t server, int64_t *queued, int64_t *in_flight, int64_t *in_flight_bytes,
+                           int64_t *peak_in_flight_bytes);
+mpm_status mpm_server_destroy(mpm_server_t server);
 
 /* Elastic energy sum_p V_p psi(F_p) of a particle set, computed without any
  * device allocation.  The paper has no counterpart: this serves callers that

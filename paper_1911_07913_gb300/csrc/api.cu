@@ -433,7 +433,8 @@ mpm_status mpm_create_scene(const mpm_scene_desc *d, const mpm_solver_opts *o, m
       if (d->grid_dims[k] < 8 || d->grid_dims[k] > 4096) fail(MPM_ERR_INVALID_ARG, "grid_dims must be in 8..4096");
     for (int k = 0; k < d->n_materials; ++k) {
       const mpm_material &m = d->materials[k];
-      if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || (m.model != 0 && m.model != 1))
+      if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || (m.model != 0 && m.model != 1) ||
+          m.plasticity < 0 || m.plasticity > 2 || (m.plasticity == 1 && !(m.yield_stress > 0.0)))
         fail(MPM_ERR_INVALID_ARG, "bad material " + std::to_string(k));
     }
     Scene *s = new Scene();
@@ -469,7 +470,8 @@ mpm_status mpm_create_scene(const mpm_scene_desc *d, const mpm_solver_opts *o, m
         mt[k].xi = std::sqrt(3.0 * (2.0 * mt[k].mu + mt[k].lam) * (2.0 * mt[k].mu + mt[k].lam) +
                              6.0 * mt[k].lam * mt[k].lam);
         mt[k].model = d->materials[k].model;
-        mt[k].pad = 0;
+        mt[k].plastic = d->materials[k].plasticity;
+        mt[k].yield = d->materials[k].yield_stress;
       }
       s->mat_table.ensure(mt.size(), 1.0);
       HOT_CUDA(cudaMemcpyAsync(s->mat_table.p, mt.data(), sizeof(MatParams) * mt.size(), cudaMemcpyHostToDevice, s->st));
@@ -604,7 +606,10 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
     });
   for (auto &t : th) t.join();
   for (int i = 0; i < n; ++i)
-    if (res[i] != MPM_OK) return res[i];
+    if (res[i] != MPM_OK) {
+      g_last_error = "scene " + std::to_string(i) + ": " + reinterpret_cast<Scene *>(scenes[i])->last_error;
+      return res[i];
+    }
   return MPM_OK;
 }
 

@@ -258,10 +258,47 @@ __device__ void svd3(const T *F, T *U, T s[3], T *V) {
 // materials
 // ---------------------------------------------------------------------------
 struct MatParams {
-  double mu, lam, xi;
-  int model;  // 0 FCR, 1 NH
-  int pad;
+  double mu, lam, xi, yield;
+  int model;    // 0 FCR, 1 NH
+  int plastic;  // 0 none, 1 von Mises, 2 snow clamp
 };
+
+// Lagged plastic projection of F after the F update (once per step):
+// 1 von Mises on the principal Hencky strains e = ln s, deviatoric part d
+//   scaled onto 2 mu |d| = yield when it exceeds it (det F unchanged);
+// 2 singular values clamped into [0.99, 1.001].  F unchanged otherwise.
+__device__ inline void plastic_project(double *F, double mu, double yield, int type) {
+  if (type == 0) return;
+  double U[9], s[3], V[9];
+  svd3<double>(F, U, s, V);
+  double sn[3];
+  if (type == 1) {
+    double e[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e[k] = log(fmax(s[k], 1e-300));
+    const double mean = (e[0] + e[1] + e[2]) / 3.0;
+    const double d0 = e[0] - mean, d1 = e[1] - mean, d2 = e[2] - mean;
+    const double nd = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    if (!(2.0 * mu * nd > yield)) return;
+    const double sc = yield / fmax(2.0 * mu * nd, 1e-300);
+    sn[0] = exp(mean + d0 * sc);
+    sn[1] = exp(mean + d1 * sc);
+    sn[2] = exp(mean + d2 * sc);
+  } else {
+    bool changed = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sn[k] = fmin(fmax(s[k], 0.99), 1.001);
+      changed = changed || sn[k] != s[k];
+    }
+    if (!changed) return;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      F[3 * i + j] = U[3 * i] * sn[0] * V[3 * j] + U[3 * i + 1] * sn[1] * V[3 * j + 1] + U[3 * i + 2] * sn[2] * V[3 * j + 2];
+}
 
 // energy density; +inf for Neo-Hookean with J <= 0
 template <class T>

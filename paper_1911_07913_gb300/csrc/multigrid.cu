@@ -9,6 +9,8 @@
 
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 namespace hot {
 
 namespace {
@@ -570,6 +572,7 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
 // ---------------------------------------------------------------------------
 constexpr int CL = 8;
 constexpr int CNT = 512;
+constexpr size_t CL_SMEM_MAX = 200 * 1024;
 struct ClusterPlan {
   int bounds[CL + 1];
 };
@@ -847,8 +850,13 @@ void plan_cluster(Scene &s, Hier<T> &h, int m) {
   }
   size_t bytes = 2 * CL * sizeof(double) + sizeof(T) * (3 * (size_t)R + 5 * 3 * (size_t)rows_max + 9 * (size_t)nb_max) +
                  sizeof(int) * ((size_t)rows_max + 1 + nb_max) + 64;
-  if (bytes > 200 * 1024) return;
-  HOT_CUDA(cudaFuncSetAttribute(k_coarse_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  if (bytes > CL_SMEM_MAX) return;
+  // set once, to the maximum: scenes planned on other threads launch the same kernel
+  static std::once_flag once;
+  std::call_once(once, [] {
+    HOT_CUDA(cudaFuncSetAttribute(k_coarse_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CL_SMEM_MAX));
+  });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(CNT);

@@ -102,7 +102,7 @@ extern "C" mpm_status mpm_particle_energy_noalloc(const double *F, const double 
       fail(MPM_ERR_INVALID_ARG, "between 1 and 16 materials are required");
     if (!energy || (n_particles > 0 && (!F || !vol))) fail(MPM_ERR_INVALID_ARG, "NULL argument");
     MatTable mt;
-    for (int k = 0; k < NA_MAX_MATERIALS; ++k) mt.m[k] = MatParams{0.0, 0.0, 0.0, 0, 0};
+    for (int k = 0; k < NA_MAX_MATERIALS; ++k) mt.m[k] = MatParams{0.0, 0.0, 0.0, 0.0, 0, 0};
     for (int k = 0; k < n_materials; ++k) {
       const double E = materials[k].E, nu = materials[k].nu;
       if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5) || (materials[k].model != 0 && materials[k].model != 1))

@@ -368,15 +368,16 @@ __global__ void k_speed_max(const double *__restrict__ pd, int64_t np, double *_
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_g2p(double *__restrict__ pd, int64_t np, GeoArgs g, const int *__restrict__ map,
-                      const double *__restrict__ vn, double dt) {
+__global__ void k_g2p(double *__restrict__ pd, const int *__restrict__ pmat, const MatParams *__restrict__ mt,
+                      int64_t np, GeoArgs g, const int *__restrict__ map, const double *__restrict__ vn,
+                      double dt) {
   int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (p >= np) return;
   double fx[3], w[3][3], dw[3][3];
   int b[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    b[k] = base_axis(pd[(PF_X + k) * np + p], g.o[k], g.inv_dx, &fx[k]);
+    b[k] = clampi(base_axis(pd[(PF_X + k) * np + p], g.o[k], g.inv_dx, &fx[k]), 0, g.dims[k] - 2);
     bspline_axis<double>(fx[k], g.inv_dx, w[k], dw[k]);
   }
   double vp[3] = {0, 0, 0}, B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -410,6 +411,8 @@ __global__ void k_g2p(double *__restrict__ pd, int64_t np, GeoArgs g, const int 
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       Fn[3 * a + c] = F[3 * a + c] + dt * (L[3 * a] * F[c] + L[3 * a + 1] * F[3 + c] + L[3 * a + 2] * F[6 + c]);
+  const MatParams mp = mt[pmat[p]];
+  plastic_project(Fn, mp.mu, mp.yield, mp.plastic);
   const double Dinv = 4.0 * g.inv_dx * g.inv_dx;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -506,7 +509,8 @@ void g2p_transfer(Scene &s, const double *vnew) {
   GeoArgs g = geo_args(s);
   if (s.np == 0) return;
   ProfScope prof_(s, "g2p");
-  k_g2p<<<(unsigned)((s.np + NT - 1) / NT), NT, 0, s.st>>>(s.pd.p, s.np, g, s.topo[0].map.p, vnew, s.dt);
+  k_g2p<<<(unsigned)((s.np + NT - 1) / NT), NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, g,
+                                                           s.topo[0].map.p, vnew, s.dt);
   HOT_LAUNCH("k_g2p");
 }
 

@@ -28,7 +28,8 @@ EXPORTED = ["mpm_set_allocator", "mpm_create_scene", "mpm_destroy_scene", "mpm_l
             "mpm_step", "mpm_get_state", "mpm_set_state", "mpm_get_grid", "mpm_eval_energy",
             "mpm_eval_gradient", "mpm_get_hessian", "mpm_apply_vcycle", "mpm_get_trace",
             "mpm_scene_footprint", "mpm_step_batch", "mpm_profile", "mpm_profile_read",
-            "mpm_kernel_launch_count", "mpm_particle_energy_noalloc"]
+            "mpm_kernel_launch_count", "mpm_particle_energy_noalloc", "mpm_server_create",
+            "mpm_server_submit", "mpm_server_poll", "mpm_server_info", "mpm_server_destroy"]
 
 
 class mpm_material(C.Structure):
@@ -128,6 +129,12 @@ def load(install_torch_allocator: bool = True):
                                      C.c_void_p]
     lib.mpm_kernel_launch_count.restype = C.c_int64
     lib.mpm_kernel_launch_count.argtypes = []
+    lib.mpm_server_create.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_void_p)]
+    lib.mpm_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    lib.mpm_server_poll.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(mpm_step_stats),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+    lib.mpm_server_info.argtypes = [C.c_void_p] + [C.POINTER(C.c_int64)] * 4
+    lib.mpm_server_destroy.argtypes = [C.c_void_p]
     lib.mpm_particle_energy_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(mpm_material),
                                                 C.c_int32, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p]
     _lib = lib
@@ -403,6 +410,53 @@ def particle_energy_noalloc(F_dev: int, vol_dev: int, mat_dev: int, materials, n
     if code != OK:
         raise HotError(code, lib.mpm_last_error(None).decode())
     return None
+
+
+class StepServer:
+    """Continuous-batching server of implicit steps for resident scenes
+    (mpm_server_* in the C ABI)."""
+
+    def __init__(self, budget_bytes: int, n_workers: int = 8):
+        self.lib = load()
+        h = C.c_void_p()
+        code = self.lib.mpm_server_create(int(budget_bytes), int(n_workers), C.byref(h))
+        if code != OK:
+            raise HotError(code, "mpm_server_create")
+        self.h = h
+
+    def submit(self, scene: "HotScene", request_id: int):
+        code = self.lib.mpm_server_submit(self.h, scene.h, int(request_id))
+        if code != OK:
+            raise HotError(code, f"request {request_id} not admitted")
+
+    def poll(self, wait: bool = True):
+        rid = C.c_int64()
+        st = mpm_step_stats()
+        lat, qd = C.c_double(), C.c_double()
+        code = C.c_int32()
+        self.lib.mpm_server_poll(self.h, 1 if wait else 0, C.byref(rid), C.byref(st), C.byref(lat), C.byref(qd),
+                                 C.byref(code))
+        if rid.value < 0:
+            return None
+        out = stats_dict(st)
+        out.update({"request_id": rid.value, "latency_s": lat.value, "queue_s": qd.value, "code": code.value})
+        return out
+
+    def info(self) -> dict:
+        v = [C.c_int64() for _ in range(4)]
+        self.lib.mpm_server_info(self.h, *[C.byref(x) for x in v])
+        return dict(zip(("queued", "in_flight", "in_flight_bytes", "peak_in_flight_bytes"), [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernel_launch_count() -> int:

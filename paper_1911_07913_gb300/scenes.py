@@ -241,6 +241,59 @@ def stretched_box_scene(seed: int = 0, res: int = 32, side: int = 8, E: float = 
                      origin, (res, res, res), (0.0, 0.0, 0.0), [], f"stretched{side}", F=F)
 
 
+def batch_scenes(seed: int = 0, count: int = 64, n_min: int = 5000, n_max: int = 200_000,
+                 E_range=(1e4, 1e8), yield_stress: float = 1e4) -> List[Scene]:
+    """Independent boxes for batched stepping: particle counts log-uniform in
+    [n_min, n_max] (8 per cell, aspect ratios in [1/2, 2]), a grid drawn from
+    64^3, 96^3, 128^3 among those that fit the box with a 5-cell margin, FCR
+    with E log-uniform in E_range, nu = 0.3, rho = 1000; every second scene
+    von Mises with the given yield stress; random velocity, sticky floor."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        target = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        cells = max(8.0, target / 8.0)
+        a = rng.uniform(0.5, 2.0, size=3)
+        a /= np.cbrt(a.prod())
+        side = np.maximum(2, np.round(a * np.cbrt(cells)).astype(int))
+        fits = [r for r in (64, 96, 128) if side.max() + 10 <= r] or [128]
+        res = int(fits[int(rng.integers(len(fits)))])
+        side = np.minimum(side, res - 10)
+        lo = np.array([(res - side[0]) // 2, 5, (res - side[2]) // 2])
+        dx = 1.0 / res
+        x = _jittered_block(rng, lo, lo + side, dx, np.zeros(3))
+        v = rng.uniform(-0.3, 0.3, size=x.shape)
+        E = float(np.exp(rng.uniform(np.log(E_range[0]), np.log(E_range[1]))))
+        plastic = k % 2
+        mats = [Material(E, 0.3, 1000.0, MODEL_FCR, plastic, yield_stress if plastic else 0.0)]
+        big = 1e30
+        bcs = [BoundaryBox(BC_STICKY, (-big, -big, -big), (big, 4.5 * dx, big))]
+        out.append(_assemble(x, v, np.zeros(x.shape[0], np.int32), mats, dx, 8, np.zeros(3),
+                             (res, res, res), (0.0, -9.8, 0.0), bcs, f"batch{k}_n{x.shape[0]}_r{res}"))
+    return out
+
+
+def serving_scenes(seed: int = 0, count: int = 256, median: float = 50_000, sigma: float = 1.0,
+                   n_max: int = 1_000_000) -> List[Scene]:
+    """Resident scenes for the step server: particle counts lognormal (median
+    50k, sigma 1, clipped at 1M), boxes as in batch_scenes, materials mixed:
+    E log-uniform in [1e4, 1e9], FCR or Neo-Hookean, every third scene von
+    Mises (yield 1e4 Pa)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = float(min(n_max, max(1000.0, np.exp(rng.normal(np.log(median), sigma)))))
+        sc = batch_scenes(seed=int(rng.integers(1 << 31)), count=1, n_min=n, n_max=n,
+                          E_range=(1e4, 1e9))[0]
+        m = sc.materials[0]
+        plastic = 1 if k % 3 == 0 else 0
+        model = int(rng.integers(2))
+        sc.materials = [Material(m.E, m.nu, m.rho, model, plastic, 1e4 if plastic else 0.0)]
+        sc.name = f"serve{k}_n{sc.n}"
+        out.append(sc)
+    return out
+
+
 def scene_by_name(name: str, seed: int = 0) -> Scene:
     if name == "cube8k":
         return cube_scene(seed)

@@ -33,7 +33,17 @@ def make_scenes():
     }
 
 
+def plastic_cube(seed, plastic, yield_stress):
+    sc = scenes.cube_scene(seed=seed, res=16, cube_lo=(5, 4, 5), side=4, vel_amp=2.0)
+    m = sc.materials[0]
+    sc.materials = [scenes.Material(m.E, m.nu, m.rho, m.model, plastic, yield_stress)]
+    return sc
+
+
 SCENES = make_scenes()
+SCENES["cube_von_mises"] = (plastic_cube(8, 1, 50.0),
+                            scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=4e-3, levels=2))
+SCENES["cube_snow"] = (plastic_cube(9, 2, 0.0), scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=4e-3, levels=2))
 
 
 def rel(a, b):
@@ -237,3 +247,78 @@ def test_state_round_trip_and_order(hot):
     s2 = g.get_state()
     g.set_state(x=s2["x"] + 0.0)
     assert np.array_equal(g.get_state()["x"], s2["x"])
+
+
+def test_plasticity_actually_projects(hot):
+    """The plastic cubes leave the elastic range in one step, so the replay
+    parity above exercises the projection."""
+    for name in ("cube_von_mises", "cube_snow"):
+        sc, opts = SCENES[name]
+        ref, info = O.hot_step(sc, opts)
+        F_el = (np.eye(3)[None] + info["dt"] * info["problem"].velocity_gradient(info["v_new"])) @ sc.F
+        assert np.abs(ref.F - F_el).max() > 1e-6, name
+
+
+def test_batch_results_match_individual_steps(hot):
+    """A scene's step is the same alone and inside a batch of concurrently
+    stepped scenes (each on its own stream)."""
+    batch = scenes.batch_scenes(seed=4, count=6, n_min=2000, n_max=20000)
+    # FP64: the only order dependence left is that of FP64 atomics (~1e-16),
+    # so the decision paths coincide and the states agree closely
+    opts = scenes.SolverOptions(eps=1e-6, cn_mode=0, levels=3, precision=0, dt=2e-3)
+    alone = []
+    for sc in batch:
+        g = hot.HotScene(sc, opts)
+        g.step()
+        alone.append(g.get_state())
+        g.close()
+    gs = [hot.HotScene(sc, opts) for sc in batch]
+    stats = hot.step_batch(gs)
+    assert all(st["status"] == 0 for st in stats)
+    for g, a in zip(gs, alone):
+        b = g.get_state()
+        assert rel(b["x"], a["x"]) < 1e-12
+        assert rel(b["v"], a["v"]) < 1e-9
+        g.close()
+
+
+def test_server_results_match_alone_and_admission(hot):
+    """Serving: step requests for several resident scenes, submitted in an
+    interleaved order and run concurrently by the server, give each scene the
+    same state as stepping it alone; a scene larger than the budget is not
+    admitted."""
+    batch = scenes.batch_scenes(seed=5, count=5, n_min=2000, n_max=20000)
+    opts = scenes.SolverOptions(eps=1e-6, cn_mode=0, levels=3, precision=0, dt=2e-3)
+    steps = [2, 1, 3, 2, 1]
+    alone = []
+    for sc, k in zip(batch, steps):
+        g = hot.HotScene(sc, opts)
+        for _ in range(k):
+            g.step()
+        alone.append(g.get_state())
+        g.close()
+    gs = [hot.HotScene(sc, opts) for sc in batch]
+    srv = hot.StepServer(budget_bytes=64 << 30, n_workers=3)
+    order = [i for r in range(3) for i in range(5) if steps[i] > r]
+    for rid, i in enumerate(order):
+        srv.submit(gs[i], rid)
+    seen = []
+    while True:
+        out = srv.poll(wait=True)
+        if out is None:
+            break
+        assert out["code"] == 0 and out["latency_s"] >= out["queue_s"] >= 0.0
+        seen.append(out["request_id"])
+    assert sorted(seen) == list(range(len(order)))
+    for g, a in zip(gs, alone):
+        b = g.get_state()
+        assert rel(b["x"], a["x"]) < 1e-12
+        assert rel(b["v"], a["v"]) < 1e-9
+    tiny = hot.StepServer(budget_bytes=1024, n_workers=1)
+    with pytest.raises(hot.HotError) as e:
+        tiny.submit(gs[0], 0)
+    assert e.value.code == 7
+    tiny.close()
+    srv.close()
+    for g in gs:
+        g.close()
