@@ -5,6 +5,7 @@
 // matrix storage"); row i stores entry e (3a+b) of its k-th block at
 // vals[9*row_ptr[i] + e*nb_i + k], so that a warp reading one entry of 32
 // consecutive blocks touches 32 consecutive words.
+#include <atomic>
 #include "internal.h"
 
 #include <cooperative_groups.h>
@@ -304,27 +305,51 @@ __global__ void k_color_fill(int64_t n, const int *__restrict__ coords, int *__r
 constexpr int RL = 32;
 constexpr int RPW = 32 / RL;   // rows per warp
 
+// Partial sums of (H u)_i over the blocks this lane visits, as explicit FMA
+// chains (the FP64 pipe is the bound of these kernels: 9 FMA per block).
+template <class T, bool LDCG = false>
+__device__ __forceinline__ void row_partial(int64_t i, bool valid, int lane, const int *__restrict__ row_ptr,
+                                            const int *__restrict__ cols, const T *__restrict__ vals,
+                                            const T *u, bool skip_diag, T acc[3]) {
+  acc[0] = acc[1] = acc[2] = T(0);
+  if (!valid) return;
+  const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
+  const T *v = vals + 9 * (int64_t)rp;
+#pragma unroll 2
+  for (int b = lane; b < nb; b += RL) {
+    int j = cols[rp + b];
+    T h[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) h[e] = v[e * nb + b];
+    if (skip_diag && j == i) continue;
+    T u0, u1, u2;
+    if (LDCG) {   // written by other SMs during this launch: read through L2
+      u0 = __ldcg(u + 3 * j);
+      u1 = __ldcg(u + 3 * j + 1);
+      u2 = __ldcg(u + 3 * j + 2);
+    } else {
+      u0 = u[3 * j];
+      u1 = u[3 * j + 1];
+      u2 = u[3 * j + 2];
+    }
+    acc[0] = fma(h[0], u0, acc[0]);
+    acc[1] = fma(h[3], u0, acc[1]);
+    acc[2] = fma(h[6], u0, acc[2]);
+    acc[0] = fma(h[1], u1, acc[0]);
+    acc[1] = fma(h[4], u1, acc[1]);
+    acc[2] = fma(h[7], u1, acc[2]);
+    acc[0] = fma(h[2], u2, acc[0]);
+    acc[1] = fma(h[5], u2, acc[1]);
+    acc[2] = fma(h[8], u2, acc[2]);
+  }
+}
+
+// (H u)_i summed over the warp, result in every lane (all three components).
 template <class T>
 __device__ __forceinline__ void row_product(int64_t i, bool valid, int lane, const int *__restrict__ row_ptr,
                                             const int *__restrict__ cols, const T *__restrict__ vals,
                                             const T *u, bool skip_diag, T acc[3]) {
-  acc[0] = acc[1] = acc[2] = T(0);
-  if (valid) {
-    const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
-    const T *v = vals + 9 * (int64_t)rp;
-#pragma unroll 2
-    for (int b = lane; b < nb; b += RL) {
-      int j = cols[rp + b];
-      T h[9];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) h[e] = v[e * nb + b];
-      if (skip_diag && j == i) continue;
-      T u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
-      acc[0] += h[0] * u0 + h[1] * u1 + h[2] * u2;
-      acc[1] += h[3] * u0 + h[4] * u1 + h[5] * u2;
-      acc[2] += h[6] * u0 + h[7] * u1 + h[8] * u2;
-    }
-  }
+  row_partial<T>(i, valid, lane, row_ptr, cols, vals, u, skip_diag, acc);
 #pragma unroll
   for (int o = RL / 2; o > 0; o >>= 1) {
     acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
@@ -333,25 +358,55 @@ __device__ __forceinline__ void row_product(int64_t i, bool valid, int lane, con
   }
 }
 
-// one color of a Gauss-Seidel sweep: u_i <- D_i^{-1} (b_i - sum_{j != i} H_ij u_j)
+// Warp sum of three per-lane values with 6 additions instead of 15: the
+// halves first trade components (lanes 0-15 keep 0 and 1, lanes 16-31 keep
+// 2), then lanes 0-7 / 8-15 split 0 and 1.  Lanes 0-7 return the sum of
+// component 0, lanes 8-15 of component 1, lanes 16-31 of component 2.
+template <class T>
+__device__ __forceinline__ T warp_sum3_split(const T a[3], int lane) {
+  const bool up = lane & 16, b3 = lane & 8;
+  const T r0 = __shfl_xor_sync(0xffffffffu, up ? a[0] : a[2], 16);
+  const T r1 = __shfl_xor_sync(0xffffffffu, a[1], 16);
+  const T x = (up ? a[2] : a[0]) + r0;   // lanes 0-15: component 0; 16-31: component 2
+  const T y = a[1] + r1;                 // lanes 0-15: component 1
+  T keep = (!up && b3) ? y : x;
+  const T send = (!up && !b3) ? y : x;
+  keep += __shfl_xor_sync(0xffffffffu, send, 8);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 4);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+  return keep;
+}
+
+// one row of a Gauss-Seidel color: u_i <- D_i^{-1} (b_i - sum_{j != i} H_ij u_j)
+// (one warp per row; lanes 0, 8, 16 form the three residual components and
+// lanes 0-2 apply the three rows of D_i^{-1})
+template <class T, bool LDCG = false>
+__device__ __forceinline__ void sgs_row(int64_t i, int lane, const int *__restrict__ row_ptr,
+                                        const int *__restrict__ cols, const T *__restrict__ vals,
+                                        const T *__restrict__ dinv, const T *__restrict__ b, T *u) {
+  static_assert(RL == 32, "one warp per row");
+  T acc[3];
+  row_partial<T, LDCG>(i, true, lane, row_ptr, cols, vals, u, true, acc);
+  const T sum = warp_sum3_split<T>(acc, lane);
+  T y = T(0);
+  if ((lane & 7) == 0 && lane < 24) y = b[3 * i + (lane >> 3)] - sum;
+  const T y0 = __shfl_sync(0xffffffffu, y, 0), y1 = __shfl_sync(0xffffffffu, y, 8),
+          y2 = __shfl_sync(0xffffffffu, y, 16);
+  if (lane < 3) {
+    const T *D = dinv + 9 * i + 3 * lane;
+    u[3 * i + lane] = fma(D[2], y2, fma(D[1], y1, D[0] * y0));
+  }
+}
+
+// one color of a sweep, one launch
 template <class T>
 __global__ void k_sgs_color(const int *__restrict__ list, int nrows, const int *__restrict__ row_ptr,
                             const int *__restrict__ cols, const T *__restrict__ vals, const T *__restrict__ dinv,
                             const T *__restrict__ b, T *u) {
-  const int warp = blockIdx.x * WPB + (threadIdx.x >> 5);
-  if (warp * RPW >= nrows) return;   // warp-uniform
-  const int g = warp * RPW + ((threadIdx.x & 31) / RL), lane = threadIdx.x % RL;
-  const bool valid = g < nrows;
-  const int64_t i = valid ? list[g] : 0;
-  T acc[3];
-  row_product<T>(i, valid, lane, row_ptr, cols, vals, u, true, acc);
-  if (valid && lane == 0) {
-    T y0 = b[3 * i] - acc[0], y1 = b[3 * i + 1] - acc[1], y2 = b[3 * i + 2] - acc[2];
-    const T *D = dinv + 9 * i;
-    u[3 * i] = D[0] * y0 + D[1] * y1 + D[2] * y2;
-    u[3 * i + 1] = D[3] * y0 + D[4] * y1 + D[5] * y2;
-    u[3 * i + 2] = D[6] * y0 + D[7] * y1 + D[8] * y2;
-  }
+  const int g = blockIdx.x * WPB + (threadIdx.x >> 5);
+  if (g >= nrows) return;   // warp-uniform
+  sgs_row<T>(list[g], threadIdx.x & 31, row_ptr, cols, vals, dinv, b, u);
 }
 
 // r = b - H u
@@ -359,17 +414,16 @@ template <class T>
 __global__ void k_residual(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ cols,
                            const T *__restrict__ vals, const T *__restrict__ b, const T *__restrict__ u,
                            T *__restrict__ r) {
-  const int64_t warp = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
-  if (warp * RPW >= n) return;
-  const int64_t i = warp * RPW + ((threadIdx.x & 31) / RL);
-  const int lane = threadIdx.x % RL;
-  const bool valid = i < n;
+  static_assert(RL == 32, "one warp per row");
+  const int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+  if (i >= n) return;   // warp-uniform
+  const int lane = threadIdx.x & 31;
   T acc[3];
-  row_product<T>(i, valid, lane, row_ptr, cols, vals, u, false, acc);
-  if (valid && lane == 0) {
-    r[3 * i] = b[3 * i] - acc[0];
-    r[3 * i + 1] = b[3 * i + 1] - acc[1];
-    r[3 * i + 2] = b[3 * i + 2] - acc[2];
+  row_partial<T>(i, true, lane, row_ptr, cols, vals, u, false, acc);
+  const T sum = warp_sum3_split<T>(acc, lane);
+  if ((lane & 7) == 0 && lane < 24) {
+    const int64_t k = 3 * i + (lane >> 3);
+    r[k] = b[k] - sum;
   }
 }
 
@@ -477,6 +531,161 @@ __device__ bool grid_sync(unsigned *bar, unsigned &gen, int *err) {
   gen += 1;
   __syncthreads();
   return ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// A whole symmetric Gauss-Seidel smoothing of one level (forward colors, then
+// backward) in one cooperative launch, with a grid barrier between colors.
+// The color order and the per-row arithmetic are those of the one-launch-
+// per-color path (the results are bitwise the same); only the launch
+// boundaries become barriers.  On levels with few rows per color the time of
+// a color is a chain of memory latencies, not work, so:
+//  - rows are dealt round-robin over the blocks first (one SM per row while
+//    there are fewer rows than SMs);
+//  - each warp's first row of every color is found (list, row_ptr) once, at
+//    the start, and kept in shared memory;
+//  - the barrier is split: a block signals its arrival, loads the matrix
+//    row, D_i^-1 and b_i of its next color (they do not depend on u), and
+//    only then waits, so those loads overlap the other blocks' arrival.
+// ---------------------------------------------------------------------------
+struct SweepPlan {
+  int off[54];   // first entry of each step's rows in the color list
+  int nr[54];    // rows of each step
+  int steps;
+};
+
+constexpr int SW_NT = 512;
+constexpr int SW_WARPS = SW_NT / 32;
+constexpr int SW_PRE = 4;   // blocks of a row held in registers per lane (rows have <= 125)
+
+template <class T>
+struct RowRegs {
+  int j[SW_PRE];
+  T h[SW_PRE][9];
+  T bv;      // lanes 0, 8, 16: component lane/8 of b_i
+  T d[3];    // lanes 0-2: row `lane` of D_i^-1
+};
+
+template <class T>
+__device__ __forceinline__ void load_row(RowRegs<T> &R, int64_t i, int rp, int nb, int lane,
+                                         const int *__restrict__ cols, const T *__restrict__ vals,
+                                         const T *__restrict__ dinv, const T *__restrict__ b) {
+  const T *v = vals + 9 * (int64_t)rp;
+#pragma unroll
+  for (int q = 0; q < SW_PRE; ++q) {
+    const int e0 = lane + 32 * q;
+    R.j[q] = e0 < nb ? cols[rp + e0] : -1;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R.h[q][e] = e0 < nb ? v[e * nb + e0] : T(0);
+  }
+  R.bv = ((lane & 7) == 0 && lane < 24) ? b[3 * i + (lane >> 3)] : T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) R.d[c] = lane < 3 ? dinv[9 * i + 3 * lane + c] : T(0);
+}
+
+// u_i from a row held in registers (u read through L2: other SMs wrote it)
+template <class T>
+__device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int rp, int nb, int lane,
+                                           const int *__restrict__ cols, const T *__restrict__ vals, T *u) {
+  T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < SW_PRE; ++q) {
+    const int j = R.j[q];
+    if (j < 0 || j == i) continue;
+    const T u0 = __ldcg(u + 3 * j), u1 = __ldcg(u + 3 * j + 1), u2 = __ldcg(u + 3 * j + 2);
+    acc[0] = fma(R.h[q][0], u0, acc[0]);
+    acc[1] = fma(R.h[q][3], u0, acc[1]);
+    acc[2] = fma(R.h[q][6], u0, acc[2]);
+    acc[0] = fma(R.h[q][1], u1, acc[0]);
+    acc[1] = fma(R.h[q][4], u1, acc[1]);
+    acc[2] = fma(R.h[q][7], u1, acc[2]);
+    acc[0] = fma(R.h[q][2], u2, acc[0]);
+    acc[1] = fma(R.h[q][5], u2, acc[1]);
+    acc[2] = fma(R.h[q][8], u2, acc[2]);
+  }
+  // rows longer than the register window (not produced by the 5^3 stencil)
+  const T *v = vals + 9 * (int64_t)rp;
+  for (int e0 = lane + 32 * SW_PRE; e0 < nb; e0 += 32) {
+    const int j = cols[rp + e0];
+    if (j == i) continue;
+    const T u0 = __ldcg(u + 3 * j), u1 = __ldcg(u + 3 * j + 1), u2 = __ldcg(u + 3 * j + 2);
+    acc[0] = fma(v[e0], u0, acc[0]);
+    acc[1] = fma(v[3 * nb + e0], u0, acc[1]);
+    acc[2] = fma(v[6 * nb + e0], u0, acc[2]);
+    acc[0] = fma(v[nb + e0], u1, acc[0]);
+    acc[1] = fma(v[4 * nb + e0], u1, acc[1]);
+    acc[2] = fma(v[7 * nb + e0], u1, acc[2]);
+    acc[0] = fma(v[2 * nb + e0], u2, acc[0]);
+    acc[1] = fma(v[5 * nb + e0], u2, acc[1]);
+    acc[2] = fma(v[8 * nb + e0], u2, acc[2]);
+  }
+  const T sum = warp_sum3_split<T>(acc, lane);
+  const T y = ((lane & 7) == 0 && lane < 24) ? R.bv - sum : T(0);
+  const T y0 = __shfl_sync(0xffffffffu, y, 0), y1 = __shfl_sync(0xffffffffu, y, 8),
+          y2 = __shfl_sync(0xffffffffu, y, 16);
+  if (lane < 3) u[3 * i + lane] = fma(R.d[2], y2, fma(R.d[1], y1, R.d[0] * y0));
+}
+
+__device__ __forceinline__ void bar_arrive_release(unsigned *bar) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
+}
+__device__ __forceinline__ unsigned bar_load_acquire(const unsigned *bar) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+  return v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, const int *__restrict__ list,
+                                                             const int *__restrict__ row_ptr,
+                                                             const int *__restrict__ cols, const T *__restrict__ vals,
+                                                             const T *__restrict__ dinv, const T *__restrict__ b, T *u,
+                                                             unsigned *bar, int *err) {
+  __shared__ int s_i[54][SW_WARPS], s_rp[54][SW_WARPS], s_nb[54][SW_WARPS];
+  __shared__ int s_ok;
+  const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int first = blockIdx.x + G * warp;   // this warp's first-round row of every step
+  for (int k = lane; k < plan.steps; k += 32) {
+    int i = -1, rp = 0, nb = 0;
+    if (first < plan.nr[k]) {
+      i = list[plan.off[k] + first];
+      rp = row_ptr[i];
+      nb = row_ptr[i + 1] - rp;
+    }
+    s_i[k][warp] = i;
+    s_rp[k][warp] = rp;
+    s_nb[k][warp] = nb;
+  }
+  if (threadIdx.x == 0) s_ok = 1;
+  __syncthreads();
+  RowRegs<T> R;
+  if (s_i[0][warp] >= 0) load_row<T>(R, s_i[0][warp], s_rp[0][warp], s_nb[0][warp], lane, cols, vals, dinv, b);
+  unsigned target = 0;
+  for (int k = 0; k < plan.steps; ++k) {
+    const int i = s_i[k][warp];
+    if (i >= 0) update_row<T>(R, i, s_rp[k][warp], s_nb[k][warp], lane, cols, vals, u);
+    // further rounds (more rows in this color than warps in the grid)
+    for (int g = first + G * SW_WARPS; g < plan.nr[k]; g += G * SW_WARPS)
+      sgs_row<T, true>(list[plan.off[k] + g], lane, row_ptr, cols, vals, dinv, b, u);
+    if (k + 1 == plan.steps) break;
+    __syncthreads();   // the block's updates of this color precede its arrival
+    if (threadIdx.x == 0) bar_arrive_release(bar);
+    target += (unsigned)G;
+    const int in = s_i[k + 1][warp];
+    if (in >= 0) load_row<T>(R, in, s_rp[k + 1][warp], s_nb[k + 1][warp], lane, cols, vals, dinv, b);
+    if (threadIdx.x == 0) {
+      long long spins = 0;
+      while (bar_load_acquire(bar) < target) {
+        if (!keep_waiting(spins, BARRIER_SPIN_LIMIT)) {
+          s_ok = 0;
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (!s_ok) return;
+  }
 }
 
 template <class T>
@@ -809,15 +1018,86 @@ void finalize_values(Scene &s, Hier<T> &h, int m) {
 }
 
 namespace {
+const char *const SWEEP_SCOPE[8] = {"sgs_l0", "sgs_l1", "sgs_l2", "sgs_l3", "sgs_l4", "sgs_l5", "sgs_l6", "sgs_l7"};
+
+// Symmetric Gauss-Seidel (Alg. 2): colors 0..26, then 26..0.  The backward
+// sweep leaves out its first non-empty color: it is the forward sweep's last,
+// and rows of one color are not coupled, so a second update in a row
+// recomputes the same values from the same inputs.
 template <class T>
-void sgs_sweep(Scene &s, Topo &t, Vals<T> &V, bool forward) {
-  for (int k = 0; k < 27; ++k) {
-    int c = forward ? k : 26 - k;
-    int nr = t.color_off[c + 1] - t.color_off[c];
+int persistent_blocks() {
+  static std::atomic<int> cached{-1};
+  int c = cached.load();
+  if (c < 0) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgs_persistent<T>, SW_NT, 0));
+    HOT_CUDA(cudaGetDevice(&dev));
+    HOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    c = std::max(1, std::min(per_sm, 1) * nsm);   // one block per SM
+    cached.store(c);
+  }
+  return c;
+}
+
+template <class T>
+void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const SweepPlan &plan, int max_rows) {
+  // one block per SM at most, and no more blocks than the largest color has rows
+  const int G = std::max(1, std::min(persistent_blocks<T>(), max_rows));
+  unsigned *bar = h.bar.p + 2;
+  HOT_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), s.st));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(SW_NT);
+  cfg.stream = s.st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T>, plan, (const int *)t.color_list.p,
+                              (const int *)t.row_ptr.p, (const int *)t.cols.p, (const T *)V.vals.p,
+                              (const T *)V.dinv.p, (const T *)V.b.p, V.u.p, bar, s.errflag.p));
+  note_launch("k_sgs_persistent");
+}
+
+// Symmetric Gauss-Seidel (Alg. 2): colors 0..26, then 26..0.  The backward
+// sweep leaves out its first non-empty color: it is the forward sweep's last,
+// and rows of one color are not coupled, so a second update in a row
+// recomputes the same values from the same inputs.  Coarse levels (and the
+// finest with flag bit 3) run the sweep as one cooperative launch; flag bit 2
+// keeps one launch per color everywhere.
+template <class T>
+void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
+  ProfScope sweep_(s, SWEEP_SCOPE[m & 7]);
+  SweepPlan plan;
+  plan.steps = 0;
+  int max_rows = 0;
+  bool skipped = false;
+  for (int k = 0; k < 54; ++k) {
+    const bool forward = k < 27;
+    const int c = forward ? k : 53 - k;
+    const int nr = t.color_off[c + 1] - t.color_off[c];
     if (nr == 0) continue;
+    if (!forward && !skipped) {
+      skipped = true;
+      continue;
+    }
+    plan.off[plan.steps] = t.color_off[c];
+    plan.nr[plan.steps] = nr;
+    plan.steps += 1;
+    max_rows = std::max(max_rows, nr);
+  }
+  if (plan.steps == 0) return;
+  const bool persistent = !(s.opts.flags & 4) && (m > 0 || (s.opts.flags & 8));
+  if (persistent) {
     ProfScope prof_(s, "sgs");
-    k_sgs_color<T><<<(unsigned)((nr + WPB * RPW - 1) / (WPB * RPW)), NT, 0, s.st>>>(
-        t.color_list.p + t.color_off[c], nr, t.row_ptr.p, t.cols.p, V.vals.p, V.dinv.p, V.b.p, V.u.p);
+    launch_sgs_persistent<T>(s, t, V, h, plan, max_rows);
+    return;
+  }
+  for (int k = 0; k < plan.steps; ++k) {
+    ProfScope prof_(s, "sgs");
+    k_sgs_color<T><<<(unsigned)((plan.nr[k] + WPB - 1) / WPB), NT, 0, s.st>>>(
+        t.color_list.p + plan.off[k], plan.nr[k], t.row_ptr.p, t.cols.p, V.vals.p, V.dinv.p, V.b.p, V.u.p);
     HOT_LAUNCH("k_sgs_color");
   }
 }
@@ -944,11 +1224,10 @@ void vcycle_launches(Scene &s, Hier<T> &h, const double *b_in, double *u_out) {
     Topo &t = s.topo[m];
     Vals<T> &V = h.L[m];
     HOT_CUDA(cudaMemsetAsync(V.u.p, 0, sizeof(T) * 3 * t.n, s.st));
-    sgs_sweep<T>(s, t, V, true);
-    sgs_sweep<T>(s, t, V, false);
+    sgs_symmetric<T>(s, t, V, h, m);
     {
       ProfScope prof_(s, "residual");
-      k_residual<T><<<(unsigned)((t.n + WPB * RPW - 1) / (WPB * RPW)), NT, 0, s.st>>>(
+      k_residual<T><<<(unsigned)((t.n + WPB - 1) / WPB), NT, 0, s.st>>>(
           t.n, t.row_ptr.p, t.cols.p, V.vals.p, V.b.p, V.u.p, V.r.p);
       HOT_LAUNCH("k_residual");
     }
@@ -965,8 +1244,7 @@ void vcycle_launches(Scene &s, Hier<T> &h, const double *b_in, double *u_out) {
     k_prolong_add<T><<<(unsigned)((t.n + NT - 1) / NT), NT, 0, s.st>>>(t.n, t.coords.p, c.map.p, dims_of(c),
                                                                        h.L[m + 1].u.p, V.u.p);
     HOT_LAUNCH("k_prolong_add");
-    sgs_sweep<T>(s, t, V, true);
-    sgs_sweep<T>(s, t, V, false);
+    sgs_symmetric<T>(s, t, V, h, m);
   }
   k_store_out<T><<<(unsigned)((3 * t0.n + NT - 1) / NT), NT, 0, s.st>>>(t0.n, h.L[0].u.p, s.fixed.p, u_out);
   HOT_LAUNCH("k_store_out");
@@ -981,7 +1259,7 @@ void vcycle_prepare(Scene &s, Hier<T> &h) {
   h.z.ensure(3 * n + 3);
   h.p.ensure(3 * n + 3);
   h.Ap.ensure(3 * n + 3);
-  h.bar.ensure(2);
+  h.bar.ensure(4);
   h.cg_log.ensure(4097, 1.0);
   h.part.ensure(2 * (size_t)coop_blocks<T>() + 2);
   if (h.cl_level != s.nlev - 1) plan_cluster<T>(s, h, s.nlev - 1);

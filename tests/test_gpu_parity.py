@@ -134,6 +134,28 @@ def test_vcycle_matches_oracle_with_same_coarse_count(hot, name):
     assert abs(vc2.cg_counts[0] - its) <= 1
 
 
+@pytest.mark.parametrize("flags", [4, 0, 8])
+def test_vcycle_smoothing_launch_modes(hot, flags):
+    """One launch per color (bit 2), one cooperative launch per coarse-level
+    sweep (default) and per sweep on every level (bit 3) apply the same
+    V-cycle."""
+    sc, opts = SCENES["bars_nh_cn"]
+    opts = scenes.SolverOptions(**{**opts.__dict__, "flags": flags})
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    g.build_hierarchy()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, O.step_dt(sc, opts))
+    L = O.build_hierarchy(og.coords, prob.hessian(), prob.hessian_pattern(), opts.levels)
+    rng = np.random.default_rng(4)
+    b = rng.normal(size=(prob.n, 3))
+    u, its = g.vcycle(b)
+    vc = O.VCycle(L, og.fixed, opts.eps, opts.max_coarse_cg)
+    vc.forced = [its]
+    assert rel(u, vc(b)) < 1e-9
+    g.close()
+
+
 def replay_trace(tr):
     return O.Trace(iters=tr["iters"], alphas=tr["alphas"], ls_trials=tr["ls_trials"],
                    cg_counts=tr["cg_counts"], skipped=tr["skipped"], fallback=tr["fallback"])
