@@ -116,9 +116,9 @@ typedef struct {
   int32_t flags;         /* bit 0: run the V-cycle eagerly instead of as a CUDA graph;
                             bit 1: coarsest solve by the cooperative kernel, not the cluster one;
                             bit 2: one launch per Gauss-Seidel color on every level;
-                            bit 3: one cooperative launch per sweep on the finest level too
-                            (by default the levels below the finest run each symmetric
-                            sweep as one cooperative launch); the bits change launch
+                            bit 3: one launch per color on the finest level only
+                            (by default each symmetric sweep of each level is one
+                            cooperative launch); bits 2 and 3 change launch
                             boundaries only, not the arithmetic */
   int32_t reserved;
 } mpm_solver_opts;

@@ -35,18 +35,21 @@ struct Topo {
   DBuf<int> rowcnt;          // n
   DBuf<int> color_list;      // n, grouped by color
   DBuf<int> color_cnt;       // 28
+  DBuf<int4> color_rec;      // n, (row, row_ptr[row], blocks in row, 0) in color_list order
   int color_off[28] = {0};   // host copy of the per-color offsets
   void set_stream(cudaStream_t st) {
     flag.st = st; map.st = coords.st = row_ptr.st = cols.st = slotpos.st = rowcnt.st = st;
-    mask.st = st; color_list.st = color_cnt.st = st;
+    mask.st = st; color_list.st = color_cnt.st = st; color_rec.st = st;
   }
   size_t bytes() const {
     return flag.bytes() + map.bytes() + coords.bytes() + row_ptr.bytes() + cols.bytes() +
-           slotpos.bytes() + mask.bytes() + rowcnt.bytes() + color_list.bytes() + color_cnt.bytes();
+           slotpos.bytes() + mask.bytes() + rowcnt.bytes() + color_list.bytes() + color_cnt.bytes() +
+           color_rec.bytes();
   }
   void release() {
     flag.release(); map.release(); coords.release(); row_ptr.release(); cols.release();
     slotpos.release(); mask.release(); rowcnt.release(); color_list.release(); color_cnt.release();
+    color_rec.release();
   }
 };
 

@@ -296,6 +296,16 @@ __global__ void k_color_fill(int64_t n, const int *__restrict__ coords, int *__r
   list[atomicAdd(&cursor[c], 1)] = (int)i;
 }
 
+// one 16-byte record per entry of the color list: the row, where its blocks
+// start and how many there are (one load instead of a chain of three)
+__global__ void k_color_records(int64_t n, const int *__restrict__ list, const int *__restrict__ row_ptr,
+                                int4 *__restrict__ rec) {
+  int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e >= n) return;
+  const int i = list[e], rp = row_ptr[i];
+  rec[e] = make_int4(i, rp, row_ptr[i + 1] - rp, 0);
+}
+
 // ---------------------------------------------------------------------------
 // smoothing kernels: a group of RL consecutive lanes per row.  Lanes of a
 // group read consecutive blocks of the row (entry-major storage keeps each of
@@ -307,7 +317,7 @@ constexpr int RPW = 32 / RL;   // rows per warp
 
 // Partial sums of (H u)_i over the blocks this lane visits, as explicit FMA
 // chains (the FP64 pipe is the bound of these kernels: 9 FMA per block).
-template <class T, bool LDCG = false>
+template <class T>
 __device__ __forceinline__ void row_partial(int64_t i, bool valid, int lane, const int *__restrict__ row_ptr,
                                             const int *__restrict__ cols, const T *__restrict__ vals,
                                             const T *u, bool skip_diag, T acc[3]) {
@@ -322,16 +332,7 @@ __device__ __forceinline__ void row_partial(int64_t i, bool valid, int lane, con
 #pragma unroll
     for (int e = 0; e < 9; ++e) h[e] = v[e * nb + b];
     if (skip_diag && j == i) continue;
-    T u0, u1, u2;
-    if (LDCG) {   // written by other SMs during this launch: read through L2
-      u0 = __ldcg(u + 3 * j);
-      u1 = __ldcg(u + 3 * j + 1);
-      u2 = __ldcg(u + 3 * j + 2);
-    } else {
-      u0 = u[3 * j];
-      u1 = u[3 * j + 1];
-      u2 = u[3 * j + 2];
-    }
+    const T u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
     acc[0] = fma(h[0], u0, acc[0]);
     acc[1] = fma(h[3], u0, acc[1]);
     acc[2] = fma(h[6], u0, acc[2]);
@@ -378,35 +379,100 @@ __device__ __forceinline__ T warp_sum3_split(const T a[3], int lane) {
   return keep;
 }
 
-// one row of a Gauss-Seidel color: u_i <- D_i^{-1} (b_i - sum_{j != i} H_ij u_j)
-// (one warp per row; lanes 0, 8, 16 form the three residual components and
-// lanes 0-2 apply the three rows of D_i^{-1})
-template <class T, bool LDCG = false>
-__device__ __forceinline__ void sgs_row(int64_t i, int lane, const int *__restrict__ row_ptr,
-                                        const int *__restrict__ cols, const T *__restrict__ vals,
-                                        const T *__restrict__ dinv, const T *__restrict__ b, T *u) {
-  static_assert(RL == 32, "one warp per row");
-  T acc[3];
-  row_partial<T, LDCG>(i, true, lane, row_ptr, cols, vals, u, true, acc);
-  const T sum = warp_sum3_split<T>(acc, lane);
-  T y = T(0);
-  if ((lane & 7) == 0 && lane < 24) y = b[3 * i + (lane >> 3)] - sum;
-  const T y0 = __shfl_sync(0xffffffffu, y, 0), y1 = __shfl_sync(0xffffffffu, y, 8),
-          y2 = __shfl_sync(0xffffffffu, y, 16);
-  if (lane < 3) {
-    const T *D = dinv + 9 * i + 3 * lane;
-    u[3 * i + lane] = fma(D[2], y2, fma(D[1], y1, D[0] * y0));
+// A row of the block matrix held in registers: every load of the row (its
+// blocks, D_i^-1 and b_i) is issued at once, so a row costs one memory round
+// trip for the matrix and one for the gathered u_j.
+constexpr int SW_PRE = 4;   // blocks of a row held in registers per lane (rows have <= 125)
+
+template <class T>
+struct RowRegs {
+  int j[SW_PRE];
+  T h[SW_PRE][9];
+  T bv;      // lanes 0, 8, 16: component lane/8 of b_i
+  T d[3];    // lanes 0-2: row `lane` of D_i^-1
+};
+
+template <class T>
+__device__ __forceinline__ void load_row(RowRegs<T> &R, int64_t i, int rp, int nb, int lane,
+                                         const int *__restrict__ cols, const T *__restrict__ vals,
+                                         const T *__restrict__ dinv, const T *__restrict__ b) {
+  const T *v = vals + 9 * (int64_t)rp;
+#pragma unroll
+  for (int q = 0; q < SW_PRE; ++q) {
+    const int e0 = lane + 32 * q;
+    R.j[q] = e0 < nb ? cols[rp + e0] : -1;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R.h[q][e] = e0 < nb ? v[e * nb + e0] : T(0);
   }
+  R.bv = ((lane & 7) == 0 && lane < 24) ? b[3 * i + (lane >> 3)] : T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) R.d[c] = lane < 3 ? dinv[9 * i + 3 * lane + c] : T(0);
 }
 
-// one color of a sweep, one launch
+// u_i from a row held in registers (LDCG: u read through L2, for launches in
+// which other SMs write it)
+template <class T, bool LDCG>
+__device__ __forceinline__ T ld_u(const T *p) {
+  if (LDCG) return __ldcg(p);
+  return *p;
+}
+
+template <class T, bool LDCG = true>
+__device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int rp, int nb, int lane,
+                                           const int *__restrict__ cols, const T *__restrict__ vals, T *u) {
+  T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < SW_PRE; ++q) {
+    const int j = R.j[q];
+    if (j < 0 || j == i) continue;
+    const T u0 = ld_u<T, LDCG>(u + 3 * j), u1 = ld_u<T, LDCG>(u + 3 * j + 1), u2 = ld_u<T, LDCG>(u + 3 * j + 2);
+    acc[0] = fma(R.h[q][0], u0, acc[0]);
+    acc[1] = fma(R.h[q][3], u0, acc[1]);
+    acc[2] = fma(R.h[q][6], u0, acc[2]);
+    acc[0] = fma(R.h[q][1], u1, acc[0]);
+    acc[1] = fma(R.h[q][4], u1, acc[1]);
+    acc[2] = fma(R.h[q][7], u1, acc[2]);
+    acc[0] = fma(R.h[q][2], u2, acc[0]);
+    acc[1] = fma(R.h[q][5], u2, acc[1]);
+    acc[2] = fma(R.h[q][8], u2, acc[2]);
+  }
+  // rows longer than the register window (not produced by the 5^3 stencil)
+  const T *v = vals + 9 * (int64_t)rp;
+  for (int e0 = lane + 32 * SW_PRE; e0 < nb; e0 += 32) {
+    const int j = cols[rp + e0];
+    if (j == i) continue;
+    const T u0 = ld_u<T, LDCG>(u + 3 * j), u1 = ld_u<T, LDCG>(u + 3 * j + 1), u2 = ld_u<T, LDCG>(u + 3 * j + 2);
+    acc[0] = fma(v[e0], u0, acc[0]);
+    acc[1] = fma(v[3 * nb + e0], u0, acc[1]);
+    acc[2] = fma(v[6 * nb + e0], u0, acc[2]);
+    acc[0] = fma(v[nb + e0], u1, acc[0]);
+    acc[1] = fma(v[4 * nb + e0], u1, acc[1]);
+    acc[2] = fma(v[7 * nb + e0], u1, acc[2]);
+    acc[0] = fma(v[2 * nb + e0], u2, acc[0]);
+    acc[1] = fma(v[5 * nb + e0], u2, acc[1]);
+    acc[2] = fma(v[8 * nb + e0], u2, acc[2]);
+  }
+  const T sum = warp_sum3_split<T>(acc, lane);
+  const T y = ((lane & 7) == 0 && lane < 24) ? R.bv - sum : T(0);
+  const T y0 = __shfl_sync(0xffffffffu, y, 0), y1 = __shfl_sync(0xffffffffu, y, 8),
+          y2 = __shfl_sync(0xffffffffu, y, 16);
+  if (lane < 3) u[3 * i + lane] = fma(R.d[2], y2, fma(R.d[1], y1, R.d[0] * y0));
+}
+
+// One row of a Gauss-Seidel color: u_i <- D_i^{-1} (b_i - sum_{j != i} H_ij u_j)
+// (one warp per row; lanes 0, 8, 16 form the three residual components and
+// lanes 0-2 apply the three rows of D_i^{-1}).
+// one color of a sweep, one launch (rows given by their color records)
 template <class T>
-__global__ void k_sgs_color(const int *__restrict__ list, int nrows, const int *__restrict__ row_ptr,
-                            const int *__restrict__ cols, const T *__restrict__ vals, const T *__restrict__ dinv,
-                            const T *__restrict__ b, T *u) {
+__global__ void k_sgs_color(const int4 *__restrict__ rec, int nrows, const int *__restrict__ cols,
+                            const T *__restrict__ vals, const T *__restrict__ dinv, const T *__restrict__ b, T *u) {
   const int g = blockIdx.x * WPB + (threadIdx.x >> 5);
   if (g >= nrows) return;   // warp-uniform
-  sgs_row<T>(list[g], threadIdx.x & 31, row_ptr, cols, vals, dinv, b, u);
+  const int lane = threadIdx.x & 31;
+  const int4 r = rec[g];
+  RowRegs<T> R;
+  load_row<T>(R, r.x, r.y, r.z, lane, cols, vals, dinv, b);
+  update_row<T, false>(R, r.x, r.y, r.z, lane, cols, vals, u);
 }
 
 // r = b - H u
@@ -414,12 +480,48 @@ template <class T>
 __global__ void k_residual(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ cols,
                            const T *__restrict__ vals, const T *__restrict__ b, const T *__restrict__ u,
                            T *__restrict__ r) {
-  static_assert(RL == 32, "one warp per row");
   const int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
   if (i >= n) return;   // warp-uniform
   const int lane = threadIdx.x & 31;
-  T acc[3];
-  row_partial<T>(i, true, lane, row_ptr, cols, vals, u, false, acc);
+  const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
+  const T *v = vals + 9 * (int64_t)rp;
+  int j[SW_PRE];
+  T h[SW_PRE][9];
+#pragma unroll
+  for (int q = 0; q < SW_PRE; ++q) {
+    const int e0 = lane + 32 * q;
+    j[q] = e0 < nb ? cols[rp + e0] : -1;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) h[q][e] = e0 < nb ? v[e * nb + e0] : T(0);
+  }
+  T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < SW_PRE; ++q) {
+    if (j[q] < 0) continue;
+    const T u0 = u[3 * j[q]], u1 = u[3 * j[q] + 1], u2 = u[3 * j[q] + 2];
+    acc[0] = fma(h[q][0], u0, acc[0]);
+    acc[1] = fma(h[q][3], u0, acc[1]);
+    acc[2] = fma(h[q][6], u0, acc[2]);
+    acc[0] = fma(h[q][1], u1, acc[0]);
+    acc[1] = fma(h[q][4], u1, acc[1]);
+    acc[2] = fma(h[q][7], u1, acc[2]);
+    acc[0] = fma(h[q][2], u2, acc[0]);
+    acc[1] = fma(h[q][5], u2, acc[1]);
+    acc[2] = fma(h[q][8], u2, acc[2]);
+  }
+  for (int e0 = lane + 32 * SW_PRE; e0 < nb; e0 += 32) {   // rows longer than the register window
+    const int jj = cols[rp + e0];
+    const T u0 = u[3 * jj], u1 = u[3 * jj + 1], u2 = u[3 * jj + 2];
+    acc[0] = fma(v[e0], u0, acc[0]);
+    acc[1] = fma(v[3 * nb + e0], u0, acc[1]);
+    acc[2] = fma(v[6 * nb + e0], u0, acc[2]);
+    acc[0] = fma(v[nb + e0], u1, acc[0]);
+    acc[1] = fma(v[4 * nb + e0], u1, acc[1]);
+    acc[2] = fma(v[7 * nb + e0], u1, acc[2]);
+    acc[0] = fma(v[2 * nb + e0], u2, acc[0]);
+    acc[1] = fma(v[5 * nb + e0], u2, acc[1]);
+    acc[2] = fma(v[8 * nb + e0], u2, acc[2]);
+  }
   const T sum = warp_sum3_split<T>(acc, lane);
   if ((lane & 7) == 0 && lane < 24) {
     const int64_t k = 3 * i + (lane >> 3);
@@ -556,76 +658,6 @@ struct SweepPlan {
 
 constexpr int SW_NT = 512;
 constexpr int SW_WARPS = SW_NT / 32;
-constexpr int SW_PRE = 4;   // blocks of a row held in registers per lane (rows have <= 125)
-
-template <class T>
-struct RowRegs {
-  int j[SW_PRE];
-  T h[SW_PRE][9];
-  T bv;      // lanes 0, 8, 16: component lane/8 of b_i
-  T d[3];    // lanes 0-2: row `lane` of D_i^-1
-};
-
-template <class T>
-__device__ __forceinline__ void load_row(RowRegs<T> &R, int64_t i, int rp, int nb, int lane,
-                                         const int *__restrict__ cols, const T *__restrict__ vals,
-                                         const T *__restrict__ dinv, const T *__restrict__ b) {
-  const T *v = vals + 9 * (int64_t)rp;
-#pragma unroll
-  for (int q = 0; q < SW_PRE; ++q) {
-    const int e0 = lane + 32 * q;
-    R.j[q] = e0 < nb ? cols[rp + e0] : -1;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) R.h[q][e] = e0 < nb ? v[e * nb + e0] : T(0);
-  }
-  R.bv = ((lane & 7) == 0 && lane < 24) ? b[3 * i + (lane >> 3)] : T(0);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) R.d[c] = lane < 3 ? dinv[9 * i + 3 * lane + c] : T(0);
-}
-
-// u_i from a row held in registers (u read through L2: other SMs wrote it)
-template <class T>
-__device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int rp, int nb, int lane,
-                                           const int *__restrict__ cols, const T *__restrict__ vals, T *u) {
-  T acc[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int q = 0; q < SW_PRE; ++q) {
-    const int j = R.j[q];
-    if (j < 0 || j == i) continue;
-    const T u0 = __ldcg(u + 3 * j), u1 = __ldcg(u + 3 * j + 1), u2 = __ldcg(u + 3 * j + 2);
-    acc[0] = fma(R.h[q][0], u0, acc[0]);
-    acc[1] = fma(R.h[q][3], u0, acc[1]);
-    acc[2] = fma(R.h[q][6], u0, acc[2]);
-    acc[0] = fma(R.h[q][1], u1, acc[0]);
-    acc[1] = fma(R.h[q][4], u1, acc[1]);
-    acc[2] = fma(R.h[q][7], u1, acc[2]);
-    acc[0] = fma(R.h[q][2], u2, acc[0]);
-    acc[1] = fma(R.h[q][5], u2, acc[1]);
-    acc[2] = fma(R.h[q][8], u2, acc[2]);
-  }
-  // rows longer than the register window (not produced by the 5^3 stencil)
-  const T *v = vals + 9 * (int64_t)rp;
-  for (int e0 = lane + 32 * SW_PRE; e0 < nb; e0 += 32) {
-    const int j = cols[rp + e0];
-    if (j == i) continue;
-    const T u0 = __ldcg(u + 3 * j), u1 = __ldcg(u + 3 * j + 1), u2 = __ldcg(u + 3 * j + 2);
-    acc[0] = fma(v[e0], u0, acc[0]);
-    acc[1] = fma(v[3 * nb + e0], u0, acc[1]);
-    acc[2] = fma(v[6 * nb + e0], u0, acc[2]);
-    acc[0] = fma(v[nb + e0], u1, acc[0]);
-    acc[1] = fma(v[4 * nb + e0], u1, acc[1]);
-    acc[2] = fma(v[7 * nb + e0], u1, acc[2]);
-    acc[0] = fma(v[2 * nb + e0], u2, acc[0]);
-    acc[1] = fma(v[5 * nb + e0], u2, acc[1]);
-    acc[2] = fma(v[8 * nb + e0], u2, acc[2]);
-  }
-  const T sum = warp_sum3_split<T>(acc, lane);
-  const T y = ((lane & 7) == 0 && lane < 24) ? R.bv - sum : T(0);
-  const T y0 = __shfl_sync(0xffffffffu, y, 0), y1 = __shfl_sync(0xffffffffu, y, 8),
-          y2 = __shfl_sync(0xffffffffu, y, 16);
-  if (lane < 3) u[3 * i + lane] = fma(R.d[2], y2, fma(R.d[1], y1, R.d[0] * y0));
-}
-
 __device__ __forceinline__ void bar_arrive_release(unsigned *bar) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
 }
@@ -635,44 +667,44 @@ __device__ __forceinline__ unsigned bar_load_acquire(const unsigned *bar) {
   return v;
 }
 
-template <class T>
-__global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, const int *__restrict__ list,
-                                                             const int *__restrict__ row_ptr,
+// MULTI: some color has more rows than the grid has warps (further rounds)
+template <class T, bool MULTI>
+__global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, const int4 *__restrict__ rec,
                                                              const int *__restrict__ cols, const T *__restrict__ vals,
                                                              const T *__restrict__ dinv, const T *__restrict__ b, T *u,
                                                              unsigned *bar, int *err) {
-  __shared__ int s_i[54][SW_WARPS], s_rp[54][SW_WARPS], s_nb[54][SW_WARPS];
+  __shared__ int4 s_rec[54][SW_WARPS];
   __shared__ int s_ok;
   const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int first = blockIdx.x + G * warp;   // this warp's first-round row of every step
-  for (int k = lane; k < plan.steps; k += 32) {
-    int i = -1, rp = 0, nb = 0;
-    if (first < plan.nr[k]) {
-      i = list[plan.off[k] + first];
-      rp = row_ptr[i];
-      nb = row_ptr[i + 1] - rp;
-    }
-    s_i[k][warp] = i;
-    s_rp[k][warp] = rp;
-    s_nb[k][warp] = nb;
-  }
+  for (int k = lane; k < plan.steps; k += 32)
+    s_rec[k][warp] = first < plan.nr[k] ? rec[plan.off[k] + first] : make_int4(-1, 0, 0, 0);
   if (threadIdx.x == 0) s_ok = 1;
   __syncthreads();
   RowRegs<T> R;
-  if (s_i[0][warp] >= 0) load_row<T>(R, s_i[0][warp], s_rp[0][warp], s_nb[0][warp], lane, cols, vals, dinv, b);
+  {
+    const int4 r0 = s_rec[0][warp];
+    if (r0.x >= 0) load_row<T>(R, r0.x, r0.y, r0.z, lane, cols, vals, dinv, b);
+  }
   unsigned target = 0;
   for (int k = 0; k < plan.steps; ++k) {
-    const int i = s_i[k][warp];
-    if (i >= 0) update_row<T>(R, i, s_rp[k][warp], s_nb[k][warp], lane, cols, vals, u);
+    const int4 r = s_rec[k][warp];
+    if (r.x >= 0) update_row<T, true>(R, r.x, r.y, r.z, lane, cols, vals, u);
     // further rounds (more rows in this color than warps in the grid)
-    for (int g = first + G * SW_WARPS; g < plan.nr[k]; g += G * SW_WARPS)
-      sgs_row<T, true>(list[plan.off[k] + g], lane, row_ptr, cols, vals, dinv, b, u);
+    if (MULTI) {
+      for (int g = first + G * SW_WARPS; g < plan.nr[k]; g += G * SW_WARPS) {
+        const int4 r2 = rec[plan.off[k] + g];
+        RowRegs<T> R2;
+        load_row<T>(R2, r2.x, r2.y, r2.z, lane, cols, vals, dinv, b);
+        update_row<T, true>(R2, r2.x, r2.y, r2.z, lane, cols, vals, u);
+      }
+    }
     if (k + 1 == plan.steps) break;
     __syncthreads();   // the block's updates of this color precede its arrival
     if (threadIdx.x == 0) bar_arrive_release(bar);
     target += (unsigned)G;
-    const int in = s_i[k + 1][warp];
-    if (in >= 0) load_row<T>(R, in, s_rp[k + 1][warp], s_nb[k + 1][warp], lane, cols, vals, dinv, b);
+    const int4 rn = s_rec[k + 1][warp];
+    if (rn.x >= 0) load_row<T>(R, rn.x, rn.y, rn.z, lane, cols, vals, dinv, b);
     if (threadIdx.x == 0) {
       long long spins = 0;
       while (bar_load_acquire(bar) < target) {
@@ -970,6 +1002,7 @@ void build_colors(Scene &s, int m) {
   Topo &t = s.topo[m];
   t.color_cnt.ensure(28);
   t.color_list.ensure(t.n + 1);
+  t.color_rec.ensure(t.n + 1);
   HOT_CUDA(cudaMemsetAsync(t.color_cnt.p, 0, sizeof(int) * 28, s.st));
   if (t.n == 0) {
     for (int c = 0; c < 28; ++c) t.color_off[c] = 0;
@@ -986,6 +1019,8 @@ void build_colors(Scene &s, int m) {
   HOT_CUDA(cudaMemcpyAsync(t.color_cnt.p, t.color_off, sizeof(int) * 27, cudaMemcpyHostToDevice, s.st));
   k_color_fill<<<nb, NT, 0, s.st>>>(t.n, t.coords.p, t.color_cnt.p, t.color_list.p);
   HOT_LAUNCH("k_color_fill");
+  k_color_records<<<nb, NT, 0, s.st>>>(t.n, t.color_list.p, t.row_ptr.p, t.color_rec.p);
+  HOT_LAUNCH("k_color_records");
   HOT_CUDA(cudaStreamSynchronize(s.st));   // color_off (host) must outlive the async copy
 }
 
@@ -1030,7 +1065,10 @@ int persistent_blocks() {
   int c = cached.load();
   if (c < 0) {
     int per_sm = 0, dev = 0, nsm = 0;
-    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgs_persistent<T>, SW_NT, 0));
+    int per_sm_multi = 0;
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgs_persistent<T, false>, SW_NT, 0));
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_multi, k_sgs_persistent<T, true>, SW_NT, 0));
+    per_sm = std::min(per_sm, per_sm_multi);
     HOT_CUDA(cudaGetDevice(&dev));
     HOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     c = std::max(1, std::min(per_sm, 1) * nsm);   // one block per SM
@@ -1054,18 +1092,23 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T>, plan, (const int *)t.color_list.p,
-                              (const int *)t.row_ptr.p, (const int *)t.cols.p, (const T *)V.vals.p,
-                              (const T *)V.dinv.p, (const T *)V.b.p, V.u.p, bar, s.errflag.p));
+  if (max_rows > G * SW_WARPS)
+    HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T, true>, plan, (const int4 *)t.color_rec.p,
+                                (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
+                                V.u.p, bar, s.errflag.p));
+  else
+    HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T, false>, plan, (const int4 *)t.color_rec.p,
+                                (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
+                                V.u.p, bar, s.errflag.p));
   note_launch("k_sgs_persistent");
 }
 
 // Symmetric Gauss-Seidel (Alg. 2): colors 0..26, then 26..0.  The backward
 // sweep leaves out its first non-empty color: it is the forward sweep's last,
 // and rows of one color are not coupled, so a second update in a row
-// recomputes the same values from the same inputs.  Coarse levels (and the
-// finest with flag bit 3) run the sweep as one cooperative launch; flag bit 2
-// keeps one launch per color everywhere.
+// recomputes the same values from the same inputs.  Each sweep is one
+// cooperative launch; flag bit 2 makes it one launch per color on every
+// level, bit 3 on the finest level only.
 template <class T>
 void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
   ProfScope sweep_(s, SWEEP_SCOPE[m & 7]);
@@ -1088,7 +1131,7 @@ void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
     max_rows = std::max(max_rows, nr);
   }
   if (plan.steps == 0) return;
-  const bool persistent = !(s.opts.flags & 4) && (m > 0 || (s.opts.flags & 8));
+  const bool persistent = !(s.opts.flags & 4) && (m > 0 || !(s.opts.flags & 8));
   if (persistent) {
     ProfScope prof_(s, "sgs");
     launch_sgs_persistent<T>(s, t, V, h, plan, max_rows);
@@ -1097,7 +1140,7 @@ void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
   for (int k = 0; k < plan.steps; ++k) {
     ProfScope prof_(s, "sgs");
     k_sgs_color<T><<<(unsigned)((plan.nr[k] + WPB - 1) / WPB), NT, 0, s.st>>>(
-        t.color_list.p + plan.off[k], plan.nr[k], t.row_ptr.p, t.cols.p, V.vals.p, V.dinv.p, V.b.p, V.u.p);
+        t.color_rec.p + plan.off[k], plan.nr[k], t.cols.p, V.vals.p, V.dinv.p, V.b.p, V.u.p);
     HOT_LAUNCH("k_sgs_color");
   }
 }

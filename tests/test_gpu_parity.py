@@ -136,9 +136,9 @@ def test_vcycle_matches_oracle_with_same_coarse_count(hot, name):
 
 @pytest.mark.parametrize("flags", [4, 0, 8])
 def test_vcycle_smoothing_launch_modes(hot, flags):
-    """One launch per color (bit 2), one cooperative launch per coarse-level
-    sweep (default) and per sweep on every level (bit 3) apply the same
-    V-cycle."""
+    """One launch per color (bit 2), one cooperative launch per sweep
+    (default) and per-color launches on the finest level only (bit 3) apply
+    the same V-cycle."""
     sc, opts = SCENES["bars_nh_cn"]
     opts = scenes.SolverOptions(**{**opts.__dict__, "flags": flags})
     g = hot.HotScene(sc, opts)
