@@ -39,7 +39,10 @@ __device__ __forceinline__ void stencil(const double *pd, int64_t np, int64_t p,
   }
 }
 
-// L_p = sum_i u_i grad w_ip^T (u2 added when present)
+// L_p = sum_i u_i grad w_ip^T (u2 added when present).  grad w_ip factors
+// over the axes, (dw_x w_y w_z, w_x dw_y w_z, w_x w_y dw_z), so the stencil
+// sum is taken one axis at a time (x, then y, then z): 270 FMA per particle
+// instead of 405 for the node-by-node form (the FP64 pipe bounds this kernel).
 __global__ void k_velgrad(const double *__restrict__ pd, int64_t np, G g, const int *__restrict__ map,
                           const double *__restrict__ u, const double *__restrict__ u2, double *__restrict__ L) {
   int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x;
@@ -47,27 +50,42 @@ __global__ void k_velgrad(const double *__restrict__ pd, int64_t np, G g, const 
   int b[3];
   double fx[3], w[3][3], dw[3][3];
   stencil(pd, np, p, g, b, fx, w, dw);
-  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // acc[3a + c] = L_ac
 #pragma unroll
-  for (int kz = 0; kz < 3; ++kz)
+  for (int kz = 0; kz < 3; ++kz) {
+    double tww[3] = {0, 0, 0}, twd[3] = {0, 0, 0}, tdw[3] = {0, 0, 0};
 #pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
+    for (int ky = 0; ky < 3; ++ky) {
+      double sw[3] = {0, 0, 0}, sd[3] = {0, 0, 0};
 #pragma unroll
       for (int kx = 0; kx < 3; ++kx) {
-        int idx = map[nlin(b[0] + kx, b[1] + ky, b[2] + kz, g.nd)];
+        const int idx = map[nlin(b[0] + kx, b[1] + ky, b[2] + kz, g.nd)];
         double ui[3] = {u[3 * idx], u[3 * idx + 1], u[3 * idx + 2]};
         if (u2) {
           ui[0] += u2[3 * idx];
           ui[1] += u2[3 * idx + 1];
           ui[2] += u2[3 * idx + 2];
         }
-        double gw[3] = {dw[0][kx] * w[1][ky] * w[2][kz], w[0][kx] * dw[1][ky] * w[2][kz],
-                        w[0][kx] * w[1][ky] * dw[2][kz]};
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) acc[3 * a + c] += ui[a] * gw[c];
+        for (int a = 0; a < 3; ++a) {
+          sw[a] = fma(ui[a], w[0][kx], sw[a]);
+          sd[a] = fma(ui[a], dw[0][kx], sd[a]);
+        }
       }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        tww[a] = fma(sw[a], w[1][ky], tww[a]);
+        twd[a] = fma(sw[a], dw[1][ky], twd[a]);
+        tdw[a] = fma(sd[a], w[1][ky], tdw[a]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc[3 * a] = fma(tdw[a], w[2][kz], acc[3 * a]);
+      acc[3 * a + 1] = fma(twd[a], w[2][kz], acc[3 * a + 1]);
+      acc[3 * a + 2] = fma(tww[a], dw[2][kz], acc[3 * a + 2]);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < 9; ++k) L[k * np + p] = acc[k];
 }
@@ -122,13 +140,17 @@ __global__ void k_energy(const double *__restrict__ pd, const int *__restrict__ 
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// Two-phase gradient.  Phase 1, one thread per particle: K_p = dt V_p P(F_p)
-// F^n_p^T and the particle's per-axis weights w, dw (3 axes x 3 offsets) into
-// scratch (27 doubles per particle, SoA).  Phase 2, one warp per occupied
-// cell: lane k < 27 owns stencil node k of the cell and sums K_p grad w_kp
-// over the cell's particles in registers, then adds to the grid once.  No
-// shared-memory atomics, full warps in both phases.
-constexpr int GS_K = 0, GS_W = 9, GS_D = 18, GS_N = 27;
+// Two-phase gradient.  The force on node i = b + (kx, ky, kz) of particle p
+// is f_i = K_p grad w_ip with K_p = dt V_p P(F_p) F^n_p^T; by the axis
+// factorization of grad w it is, per component a,
+//   f_i[a] = A0[a][kx] P0[ky][kz] + A1[a][kx] P1[ky][kz] + A2[a][kx] P2[ky][kz]
+// with A0 = K[a][0] dw_x, A1 = K[a][1] w_x, A2 = K[a][2] w_x and P0 = w_y w_z,
+// P1 = dw_y w_z, P2 = w_y dw_z.  Phase 1, one thread per particle: the 27 A
+// and 27 P values into scratch (SoA).  Phase 2, one warp per occupied cell:
+// lane k < 27 owns stencil node k of the cell and sums f over the cell's
+// particles in registers (9 FMA per particle), then adds to the grid once.
+// No shared-memory atomics, full warps in both phases.
+constexpr int GS_A = 0, GS_P = 27, GS_N = 54;
 __global__ void k_grad_particles(const double *__restrict__ pd, const int *__restrict__ pmat,
                                  const MatParams *__restrict__ mt, int64_t np, const double *__restrict__ Lv,
                                  double dt, G g, double *__restrict__ scr) {
@@ -138,24 +160,33 @@ __global__ void k_grad_particles(const double *__restrict__ pd, const int *__res
   double fx[3], w[3][3], dw[3][3];
   stencil(pd, np, p, g, b, fx, w, dw);
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      scr[(GS_W + 3 * a + k) * np + p] = w[a][k];
-      scr[(GS_D + 3 * a + k) * np + p] = dw[a][k];
+    for (int kz = 0; kz < 3; ++kz) {
+      scr[(GS_P + 3 * ky + kz) * np + p] = w[1][ky] * w[2][kz];
+      scr[(GS_P + 9 + 3 * ky + kz) * np + p] = dw[1][ky] * w[2][kz];
+      scr[(GS_P + 18 + 3 * ky + kz) * np + p] = w[1][ky] * dw[2][kz];
     }
   double F[9], P[9];
   deformed(pd, np, p, Lv, nullptr, 0.0, dt, F);
   const MatParams mp = mt[pmat[p]];
   piola<double>(F, mp.mu, mp.lam, mp.model, P);
   const double sc = dt * pd[PF_VOL * np + p];
+  double K[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      scr[(GS_K + 3 * a + c) * np + p] =
-          sc * (P[3 * a] * pd[(PF_F + 3 * c) * np + p] + P[3 * a + 1] * pd[(PF_F + 3 * c + 1) * np + p] +
-                P[3 * a + 2] * pd[(PF_F + 3 * c + 2) * np + p]);
+      K[3 * a + c] = sc * (P[3 * a] * pd[(PF_F + 3 * c) * np + p] + P[3 * a + 1] * pd[(PF_F + 3 * c + 1) * np + p] +
+                           P[3 * a + 2] * pd[(PF_F + 3 * c + 2) * np + p]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+      scr[(GS_A + 3 * a + kx) * np + p] = K[3 * a] * dw[0][kx];
+      scr[(GS_A + 9 + 3 * a + kx) * np + p] = K[3 * a + 1] * w[0][kx];
+      scr[(GS_A + 18 + 3 * a + kx) * np + p] = K[3 * a + 2] * w[0][kx];
+    }
 }
 
 __global__ void k_grad_cells(const double *__restrict__ scr, int64_t np, const int *__restrict__ cell_first,
@@ -165,17 +196,22 @@ __global__ void k_grad_cells(const double *__restrict__ scr, int64_t np, const i
   const int lane = threadIdx.x & 31;
   if (c >= ncell || lane >= 27) return;
   const int kx = lane % 3, ky = (lane / 3) % 3, kz = lane / 9;
+  const int yz = 3 * ky + kz;
   const int first = cell_first[c], cnt = cell_n[c];
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
   for (int q = 0; q < cnt; ++q) {
     const int64_t p = first + q;
-    const double wx = scr[(GS_W + kx) * np + p], wy = scr[(GS_W + 3 + ky) * np + p], wz = scr[(GS_W + 6 + kz) * np + p];
-    const double g0 = scr[(GS_D + kx) * np + p] * wy * wz;
-    const double g1 = wx * scr[(GS_D + 3 + ky) * np + p] * wz;
-    const double g2 = wx * wy * scr[(GS_D + 6 + kz) * np + p];
-    a0 += scr[(GS_K + 0) * np + p] * g0 + scr[(GS_K + 1) * np + p] * g1 + scr[(GS_K + 2) * np + p] * g2;
-    a1 += scr[(GS_K + 3) * np + p] * g0 + scr[(GS_K + 4) * np + p] * g1 + scr[(GS_K + 5) * np + p] * g2;
-    a2 += scr[(GS_K + 6) * np + p] * g0 + scr[(GS_K + 7) * np + p] * g1 + scr[(GS_K + 8) * np + p] * g2;
+    const double p0 = scr[(GS_P + yz) * np + p], p1 = scr[(GS_P + 9 + yz) * np + p],
+                 p2 = scr[(GS_P + 18 + yz) * np + p];
+    a0 = fma(scr[(GS_A + kx) * np + p], p0, a0);
+    a1 = fma(scr[(GS_A + 3 + kx) * np + p], p0, a1);
+    a2 = fma(scr[(GS_A + 6 + kx) * np + p], p0, a2);
+    a0 = fma(scr[(GS_A + 9 + kx) * np + p], p1, a0);
+    a1 = fma(scr[(GS_A + 12 + kx) * np + p], p1, a1);
+    a2 = fma(scr[(GS_A + 15 + kx) * np + p], p1, a2);
+    a0 = fma(scr[(GS_A + 18 + kx) * np + p], p2, a0);
+    a1 = fma(scr[(GS_A + 21 + kx) * np + p], p2, a1);
+    a2 = fma(scr[(GS_A + 24 + kx) * np + p], p2, a2);
   }
   const unsigned key = (unsigned)cell_key[c];
   const unsigned B = key >> 6, l = key & 63u;

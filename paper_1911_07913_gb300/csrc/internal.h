@@ -164,7 +164,7 @@ struct Scene {
   DBuf<double> hist_s, hist_y; // MAX_HIST x 3n
   DBuf<double> Lv, Lp;         // 9 np: sum_i u_i grad w_ip^T for v^n+dv and for p
   DBuf<double> Le, dv_e, g_e;  // scratch of the evaluation entry points
-  DBuf<double> gscr;           // 27 np: per-particle K and weight tables of the gradient
+  DBuf<double> gscr;           // 54 np: per-particle factor tables of the gradient
   DBuf<double> part;           // partial sums
   DBuf<double> scal;           // device scalars
   DBuf<int> errflag;
