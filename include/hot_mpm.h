@@ -116,7 +116,10 @@ typedef struct {
   int32_t flags;         /* bit 0: run the V-cycle eagerly instead of as a CUDA graph;
                             bit 1: coarsest solve by the cooperative kernel, not the cluster one;
                             bit 2: one launch per Gauss-Seidel color on every level;
-                            bit 3: one launch per color on the finest level only
+                            bit 3: one launch per color on the finest level only;
+                            bit 4: drive the L-BFGS iterations from the host (by default they
+                            run as one CUDA graph whose conditional nodes take every decision
+                            on the device; profiling and bit 0 also select the host loop)
                             (by default each symmetric sweep of each level is one
                             cooperative launch); bits 2 and 3 change launch
                             boundaries only, not the arithmetic */
@@ -136,8 +139,9 @@ typedef struct {
   int64_t nnz_blocks[8];   /* 3x3 blocks per level */
   int32_t n_levels;
   int32_t status;
-  int32_t graph_vcycles;   /* V-cycles replayed from a captured CUDA graph */
-  int32_t reserved;
+  int32_t graph_vcycles;   /* V-cycles run from a captured CUDA graph */
+  int32_t device_loop;     /* 1: the L-BFGS iterations ran as one CUDA graph with device-side
+                              decisions (conditional nodes); 0: host-driven loop */
 } mpm_step_stats;
 
 /* Device memory hook.  alloc(bytes, stream, ctx) returns device memory or

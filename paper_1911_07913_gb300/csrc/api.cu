@@ -29,6 +29,10 @@ void note_launch(const char *what) {
   check_cuda(cudaGetLastError(), what);
 }
 
+// kernels run by a graph launch (counted once per executed kernel node)
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 static cudaEvent_t take_event(Scene &s) {
   if (!s.ev_pool.empty()) {
     cudaEvent_t e = s.ev_pool.back();
@@ -103,7 +107,7 @@ size_t Scene::bytes() const {
              v.bytes() + xi.bytes() + fixed.bytes() + mv.bytes() + mxi.bytes() + dv.bytes() + g.bytes() +
              pdir.bytes() + q.bytes() + g_new.bytes() + dv_new.bytes() + vtmp.bytes() + hist_s.bytes() +
              hist_y.bytes() + Lv.bytes() + Lp.bytes() + Le.bytes() + dv_e.bytes() + g_e.bytes() + gscr.bytes() +
-             part.bytes() +
+             part.bytes() + tr_alpha.bytes() + tr_int.bytes() + lstate.bytes() +
              scal.bytes() + errflag.bytes() + scan.block_sums.bytes() + scan.total.bytes() + hd.bytes() + hf.bytes();
   for (auto &t : topo) b += t.bytes();
   return b;
@@ -111,10 +115,11 @@ size_t Scene::bytes() const {
 
 void Scene::release() {
   for (auto *b : {&pd, &pd_alt, &m, &v, &xi, &mv, &mxi, &dv, &g, &pdir, &q, &g_new, &dv_new, &vtmp, &hist_s,
-                  &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e, &gscr})
+                  &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e, &gscr, &tr_alpha})
     b->release();
+  lstate.release();
   for (auto *b : {&pmat, &pmat_alt, &pid, &pid_alt, &slot, &perm, &tmp, &cell_count, &cell_start, &cell_first,
-                  &cell_n, &cell_key, &blk_first, &blk_end, &blk_key, &flags, &flag_scan, &errflag})
+                  &cell_n, &cell_key, &blk_first, &blk_end, &blk_key, &flags, &flag_scan, &errflag, &tr_int})
     b->release();
   key.release();
   fixed.release();
@@ -244,7 +249,9 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   mpm_status status = MPM_OK;
   int it = 0, trials_total = 0, cg_total = 0;
   double nrm = 0.0;
-  while (true) {
+  const double thr = s.opts.cn_mode == 0 ? s.opts.eps * std::sqrt((double)nfree) : s.opts.eps * g1n;
+  const bool on_device = solve_loop_graph(s, E, norms, thr, E, nrm, it, trials_total, status);
+  while (!on_device) {
     if (!std::isfinite(norms[0]) || !std::isfinite(norms[1]) || !std::isfinite(E)) {
       status = MPM_ERR_NUMERIC;
       break;
@@ -349,6 +356,7 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   }
   out.status = status;
   out.graph_vcycles = s.graph_launches;
+  out.device_loop = on_device ? 1 : 0;
   s.last_stats = out;
   if (st) *st = out;
   return status;
@@ -522,6 +530,8 @@ mpm_status mpm_destroy_scene(mpm_scene_t sc) {
   cudaStreamSynchronize(s->st);
   s->drop_graph();
   s->release();
+  for (auto a : s->aux_st)
+    if (a) cudaStreamDestroy(a);
   if (s->own_stream) cudaStreamDestroy(s->st);
   delete s;
   return MPM_OK;

@@ -111,10 +111,11 @@ __device__ __forceinline__ void deformed(const double *pd, int64_t np, int64_t p
 // terms 1/2 m |dv + a p|^2 - dt m g.(dv + a p).  One partial per block.
 __global__ void k_energy(const double *__restrict__ pd, const int *__restrict__ pmat, const MatParams *__restrict__ mt,
                          int64_t np, const double *__restrict__ Lv, const double *__restrict__ Lp, double alpha,
-                         double dt, int nbp, int64_t nn, const double *__restrict__ m, const double *__restrict__ dv,
-                         const double *__restrict__ pdir, double g0, double g1, double g2,
-                         double *__restrict__ part) {
+                         const double *__restrict__ alpha_dev, double dt, int nbp, int64_t nn,
+                         const double *__restrict__ m, const double *__restrict__ dv, const double *__restrict__ pdir,
+                         double g0, double g1, double g2, double *__restrict__ part) {
   __shared__ double sh[NT];
+  if (alpha_dev) alpha = *alpha_dev;   // step length held on the device (device-driven loop)
   double acc = 0.0;
   if ((int)blockIdx.x < nbp) {
     for (int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x; p < np; p += (int64_t)nbp * NT) {
@@ -421,26 +422,32 @@ void velocity_gradient(Scene &s, const double *u, const double *u2, double *L) {
   HOT_LAUNCH("k_velgrad");
 }
 
-double energy(Scene &s, const double *L1, const double *L2, double alpha, const double *dvv, const double *pv) {
+int energy_launch(Scene &s, const double *L1, const double *L2, double alpha, const double *alpha_dev,
+                  const double *dvv, const double *pv) {
   const int nbp = 2 * s.nsm, nbn = s.nsm;
   s.part.ensure(4096);
+  ProfScope prof_(s, "energy");
+  k_energy<<<nbp + nbn, NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, L1, L2, alpha, alpha_dev, s.dt, nbp,
+                                       s.nn(), s.m.p, dvv, pv, s.gravity[0], s.gravity[1], s.gravity[2], s.part.p);
+  HOT_LAUNCH("k_energy");
+  return nbp + nbn;
+}
+
+double energy(Scene &s, const double *L1, const double *L2, double alpha, const double *dvv, const double *pv) {
   if (alpha == 0.0) {
     L2 = nullptr;
     pv = nullptr;
   }
-  ProfScope prof_(s, "energy");
-  k_energy<<<nbp + nbn, NT, 0, s.st>>>(s.pd.p, s.pmat.p, s.mat_table.p, s.np, L1, L2, alpha, s.dt, nbp, s.nn(), s.m.p,
-                                       dvv, pv, s.gravity[0], s.gravity[1], s.gravity[2], s.part.p);
-  HOT_LAUNCH("k_energy");
-  std::vector<double> h(nbp + nbn);
+  const int np = energy_launch(s, L1, L2, alpha, nullptr, dvv, pv);
+  std::vector<double> h(np);
   HOT_CUDA(cudaMemcpyAsync(h.data(), s.part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s.st));
   HOT_CUDA(cudaStreamSynchronize(s.st));
   double e = 0.0;
-  for (double x : h) e += x;
+  for (double x : h) e += x;   // fixed order (the device-driven loop sums in the same order)
   return e;
 }
 
-void gradient(Scene &s, const double *Lcur, const double *dvec, double *gout, double norms[2]) {
+int gradient_launch(Scene &s, const double *Lcur, const double *dvec, double *gout) {
   const int64_t nn = s.nn();
   HOT_CUDA(cudaMemsetAsync(gout, 0, sizeof(double) * 3 * nn, s.st));
   if (s.n_cells > 0) {
@@ -459,11 +466,16 @@ void gradient(Scene &s, const double *Lcur, const double *dvec, double *gout, do
   k_grad_nodes<<<nb, NT, 0, s.st>>>(nn, s.m.p, s.xi.p, s.fixed.p, dvec, s.dt, s.gravity[0], s.gravity[1],
                                     s.gravity[2], cn_scale, gout, s.part.p);
   HOT_LAUNCH("k_grad_nodes");
+  return nb;
+}
+
+void gradient(Scene &s, const double *Lcur, const double *dvec, double *gout, double norms[2]) {
+  const int nb = gradient_launch(s, Lcur, dvec, gout);
   std::vector<double> h(2 * nb);
   HOT_CUDA(cudaMemcpyAsync(h.data(), s.part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s.st));
   HOT_CUDA(cudaStreamSynchronize(s.st));
   norms[0] = norms[1] = 0.0;
-  for (int b = 0; b < nb; ++b) {
+  for (int b = 0; b < nb; ++b) {   // fixed order (the device-driven loop sums in the same order)
     norms[0] += h[2 * b];
     norms[1] += h[2 * b + 1];
   }

@@ -111,6 +111,13 @@ struct Trace {
   }
 };
 
+// Scalars of the device-driven L-BFGS loop (Alg. 3), in device memory.
+struct LoopState {
+  double E, E1, alpha, pg, n0, n1, nrm;
+  double rho[MAX_HIST];
+  int it, t, ok, fb, hist_n, head, status, trials_total;
+};
+
 struct Scene;
 // Opt-in device timing of one kernel launch (CUDA events on the scene's
 // stream around the launch); no cost when the scene's profiling is off.
@@ -169,6 +176,11 @@ struct Scene {
   DBuf<double> scal;           // device scalars
   DBuf<int> errflag;
   ScanScratch scan;
+  DBuf<LoopState> lstate;      // device-driven loop scalars
+  DBuf<double> tr_alpha;       // device-driven loop trace: step lengths
+  DBuf<int> tr_int;            // ... line-search trials | skipped pairs | fallbacks
+  cudaStream_t aux_st[2] = {nullptr, nullptr};   // streams for captures of conditional bodies
+  bool loop_graph_ok = true;
 
   int nlev = 0;
   Topo topo[MAX_LEVELS];
@@ -188,6 +200,7 @@ struct Scene {
   bool own_stream = false;
   cudaGraphExec_t vgraph = nullptr;
   const void *vgraph_b = nullptr, *vgraph_u = nullptr;
+  long long vgraph_kernels = 0;   // kernels in the captured V-cycle
   void drop_graph() {
     if (vgraph) cudaGraphExecDestroy(vgraph);
     vgraph = nullptr;
@@ -205,14 +218,15 @@ struct Scene {
   void set_stream(cudaStream_t s) {
     st = s;
     for (auto *b : {&pd, &pd_alt, &m, &v, &xi, &mv, &mxi, &dv, &g, &pdir, &q, &g_new, &dv_new, &vtmp,
-                    &hist_s, &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e, &gscr})
+                    &hist_s, &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e, &gscr, &tr_alpha})
       b->st = s;
     for (auto *b : {&pmat, &pmat_alt, &pid, &pid_alt, &slot, &perm, &tmp, &cell_count, &cell_start,
                     &cell_first, &cell_n, &cell_key, &blk_first, &blk_end, &blk_key, &flags, &flag_scan,
-                    &errflag})
+                    &errflag, &tr_int})
       b->st = s;
     key.st = s;
     fixed.st = s;
+    lstate.st = s;
     mat_table.st = s;
     bc_dev.st = s;
     scan.block_sums.st = scan.total.st = s;
@@ -241,9 +255,15 @@ void velocity_gradient(Scene &s, const double *u, const double *u2, double *L);
 // E(dv + alpha p): particles use F = (I + dt (L1 + alpha L2)) F^n, nodes use
 // dv + alpha p (L2 and p may be NULL when alpha = 0)
 double energy(Scene &s, const double *L1, const double *L2, double alpha, const double *dv, const double *p);
+// launch only: partials of the energy into s.part (returns their count); the
+// step length is read from alpha_dev when it is not NULL
+int energy_launch(Scene &s, const double *L1, const double *L2, double alpha, const double *alpha_dev,
+                  const double *dv, const double *p);
 // gradient at the state whose velocity gradient is L and node increment dvec;
 // norms_out[0] = ||g||^2, norms_out[1] = ||g^||^2 (CN-scaled), both host
 void gradient(Scene &s, const double *L, const double *dvec, double *gout, double norms_out[2]);
+// launch only: gradient into gout, norm partials (pairs) into s.part; returns the pair count
+int gradient_launch(Scene &s, const double *L, const double *dvec, double *gout);
 template <class T>
 void particle_stiffness(Scene &s, Hier<T> &h);
 template <class T>
@@ -262,6 +282,10 @@ void finalize_values(Scene &s, Hier<T> &h, int m);   // diagonal inverses
 template <class T>
 void vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, bool use_graph);
 template <class T>
+void vcycle_ready(Scene &s, Hier<T> &h);                                      // before a capture
+template <class T>
+void vcycle_emit(Scene &s, Hier<T> &h, const double *b_in, double *u_out);   // launches only
+template <class T>
 void reset_cg_log(Scene &s, Hier<T> &h);
 template <class T>
 std::vector<int> read_cg_log(Scene &s, Hier<T> &h);
@@ -279,6 +303,25 @@ int64_t count_free(Scene &s);                                                   
 // input; second half turns r (the V-cycle output) into the direction.
 void two_loop_first(Scene &s, double *q, int64_t n);
 void two_loop_second(Scene &s, double *r, int64_t n);
+// The same with the pair count, history head and rho read from a LoopState
+// on the device (a fixed launch sequence, inactive steps do nothing).
+void two_loop_first_dev(Scene &s, double *q, int64_t n, const LoopState *st);
+void two_loop_second_dev(Scene &s, double *r, int64_t n, const LoopState *st);
+// launch only: k_dot3 partials (triples, one per block) into part; returns the block count
+int dot_launch(Scene &s, const double *x, const double *y, int64_t n, int mode, double *part);
+// {y.s, y.y, s.s} partials of the history pair in slot st->head
+int dots3_hist_launch(Scene &s, int64_t n, const LoopState *st, double *part);
+void lincomb_alpha(Scene &s, double *z, const double *x, const double *y, int64_t n, const LoopState *st);  // z = x + alpha y
+void axpy_alpha(Scene &s, double *y, const double *x, int64_t n, const LoopState *st);                     // y += alpha x
+void hist_diff(Scene &s, double *base, const double *x, const double *y, int64_t n, const LoopState *st);  // slot head of base = x - y
+
+// ---- solve_graph.cu
+// Alg. 3's iterations as one CUDA graph with conditional nodes (device-side
+// decisions); returns false, touching nothing, when the graph cannot be built.
+bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double &E, double &nrm, int &it,
+                      int &trials_total, mpm_status &status);
+void note_launches(long long n);   // adds to the kernel launch counter
+long long launch_count();
 
 int read_errflag(Scene &s);
 

@@ -1305,6 +1305,7 @@ void vcycle_prepare(Scene &s, Hier<T> &h) {
   h.bar.ensure(4);
   h.cg_log.ensure(4097, 1.0);
   h.part.ensure(2 * (size_t)coop_blocks<T>() + 2);
+  persistent_blocks<T>();   // occupancy queries before any capture
   if (h.cl_level != s.nlev - 1) plan_cluster<T>(s, h, s.nlev - 1);
 }
 
@@ -1324,6 +1325,7 @@ void vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, bool use_gr
     }
     if (!s.vgraph) {
       cudaGraph_t g = nullptr;
+      const long long c0 = launch_count();
       bool ok = cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       if (ok) {
         try {
@@ -1337,6 +1339,8 @@ void vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, bool use_gr
         if (g) cudaGraphDestroy(g);
       }
       cudaGetLastError();
+      s.vgraph_kernels = launch_count() - c0;
+      note_launches(-s.vgraph_kernels);   // captured, not run
       if (!ok) {
         s.vgraph = nullptr;
         s.graphs_ok = false;   // run eagerly from now on
@@ -1347,12 +1351,24 @@ void vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, bool use_gr
     }
     if (s.vgraph) {
       HOT_CUDA(cudaGraphLaunch(s.vgraph, s.st));
-      note_launch("vcycle_graph");
+      note_launches(s.vgraph_kernels);
       ++s.graph_launches;
       return;
     }
   }
   vcycle_launches<T>(s, h, b_in, u_out);
+}
+
+// The V-cycle's launches alone, into whatever the stream is doing (a
+// capture of a larger graph included); vcycle_ready sizes its buffers and
+// plans the coarsest solve beforehand (it may synchronize).
+template <class T>
+void vcycle_ready(Scene &s, Hier<T> &h) {
+  if (s.topo[0].n > 0) vcycle_prepare<T>(s, h);
+}
+template <class T>
+void vcycle_emit(Scene &s, Hier<T> &h, const double *b_in, double *u_out) {
+  if (s.topo[0].n > 0) vcycle_launches<T>(s, h, b_in, u_out);
 }
 
 template <class T>
@@ -1383,6 +1399,10 @@ template void finalize_values<double>(Scene &, Hier<double> &, int);
 template void finalize_values<float>(Scene &, Hier<float> &, int);
 template void vcycle<double>(Scene &, Hier<double> &, const double *, double *, bool);
 template void vcycle<float>(Scene &, Hier<float> &, const double *, double *, bool);
+template void vcycle_ready<double>(Scene &, Hier<double> &);
+template void vcycle_ready<float>(Scene &, Hier<float> &);
+template void vcycle_emit<double>(Scene &, Hier<double> &, const double *, double *);
+template void vcycle_emit<float>(Scene &, Hier<float> &, const double *, double *);
 template void reset_cg_log<double>(Scene &, Hier<double> &);
 template void reset_cg_log<float>(Scene &, Hier<float> &);
 template std::vector<int> read_cg_log<double>(Scene &, Hier<double> &);

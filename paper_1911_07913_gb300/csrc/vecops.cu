@@ -14,10 +14,10 @@ __global__ void k_dot3(const double *__restrict__ x, const double *__restrict__ 
   double a = 0.0, b = 0.0, c = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT) {
     double xv = x[k], yv = y[k];
-    a += xv * yv;
+    a = __fma_rn(xv, yv, a);
     if (mode) {
-      b += xv * xv;
-      c += yv * yv;
+      b = __fma_rn(xv, xv, b);
+      c = __fma_rn(yv, yv, c);
     }
   }
   a = block_sum<NT>(a, sh);
@@ -32,12 +32,15 @@ __global__ void k_dot3(const double *__restrict__ x, const double *__restrict__ 
   }
 }
 
+// the rounding of these is spelled out so that the device-driven loop's
+// versions (scalars read on the device) give the same bits
 __global__ void k_axpy(double *__restrict__ y, double a, const double *__restrict__ x, int64_t n) {
-  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT) y[k] += a * x[k];
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT)
+    y[k] = __fma_rn(a, x[k], y[k]);
 }
 __global__ void k_lincomb(double *z, double a, const double *x, double b, const double *y, int64_t n) {
   for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT)
-    z[k] = a * x[k] + (y ? b * y[k] : 0.0);
+    z[k] = y ? __fma_rn(b, y[k], __dmul_rn(a, x[k])) : __dmul_rn(a, x[k]);
 }
 
 // Two-loop steps with the scalar coefficient formed on the device from the
@@ -46,35 +49,125 @@ __global__ void k_lincomb(double *z, double a, const double *x, double b, const 
 //   second loop: beta = rho_a y_a^T r;     r <- r + (alpha_a - beta) s_a
 // Each launch applies the update for one pair (if upd) and emits the partial
 // dot of the next pair (if nxt).
-__global__ void k_twoloop_step(double *v, const double *__restrict__ upd_vec, const double *__restrict__ part_in,
-                               int nin, double rho, double *__restrict__ alpha_store, int second,
-                               const double *__restrict__ alpha_prev, const double *__restrict__ nxt,
-                               double *__restrict__ part_out, int64_t n) {
-  __shared__ double sh[NT];
+__device__ __forceinline__ void twoloop_body(double *v, const double *__restrict__ upd_vec,
+                                             const double *__restrict__ part_in, int nin, double rho,
+                                             double *__restrict__ alpha_store, int second,
+                                             const double *__restrict__ alpha_prev, const double *__restrict__ nxt,
+                                             double *__restrict__ part_out, int64_t n, double *sh) {
   double coef = 0.0;
   if (upd_vec) {
     double S = sum_partials<NT>(part_in, nin, sh);
     if (!second) {
-      double a = rho * S;
+      double a = __dmul_rn(rho, S);
       coef = -a;
       if (blockIdx.x == 0 && threadIdx.x == 0) *alpha_store = a;
     } else {
-      coef = *alpha_prev - rho * S;
+      coef = __fma_rn(-rho, S, *alpha_prev);
     }
   }
   double acc = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT) {
     double vk = v[k];
     if (upd_vec) {
-      vk += coef * upd_vec[k];
+      vk = __fma_rn(coef, upd_vec[k], vk);
       v[k] = vk;
     }
-    if (nxt) acc += nxt[k] * vk;
+    if (nxt) acc = __fma_rn(nxt[k], vk, acc);
   }
   if (nxt) {
     acc = block_sum<NT>(acc, sh);
     if (threadIdx.x == 0) part_out[blockIdx.x] = acc;
   }
+}
+
+__global__ void k_twoloop_step(double *v, const double *__restrict__ upd_vec, const double *__restrict__ part_in,
+                               int nin, double rho, double *__restrict__ alpha_store, int second,
+                               const double *__restrict__ alpha_prev, const double *__restrict__ nxt,
+                               double *__restrict__ part_out, int64_t n) {
+  __shared__ double sh[NT];
+  twoloop_body(v, upd_vec, part_in, nin, rho, alpha_store, second, alpha_prev, nxt, part_out, n, sh);
+}
+
+// The same step with its pair taken from the device state: launch j of a
+// fixed sequence of w + 1 (j = -1 only emits the first partial); steps past
+// the current pair count do nothing.  Slot of the k-th newest pair:
+// (head - 1 - k) mod w, as on the host.
+__global__ void k_twoloop_dev(double *v, const double *__restrict__ upd_base, const double *__restrict__ nxt_base,
+                              int64_t n, int w, const LoopState *__restrict__ st, int j, int second,
+                              const double *__restrict__ part_in, int nin, double *__restrict__ part_out,
+                              double *__restrict__ alpha_base) {
+  __shared__ double sh[NT];
+  const int m = st->hist_n, head = st->head;
+  if (m == 0 || j >= m) return;
+  auto slot = [&](int k) { return ((head - 1 - k) % w + w) % w; };
+  const double *upd = nullptr, *nxt = nullptr;
+  double rho = 0.0;
+  int a = 0;
+  if (!second) {
+    if (j < 0) {
+      nxt = nxt_base + (int64_t)slot(0) * n;
+    } else {
+      a = slot(j);
+      upd = upd_base + (int64_t)a * n;
+      nxt = j + 1 < m ? nxt_base + (int64_t)slot(j + 1) * n : nullptr;
+      rho = st->rho[a];
+    }
+  } else {
+    if (j < 0) {
+      nxt = nxt_base + (int64_t)slot(m - 1) * n;
+    } else {
+      const int k = m - 1 - j;
+      a = slot(k);
+      upd = upd_base + (int64_t)a * n;
+      nxt = k - 1 >= 0 ? nxt_base + (int64_t)slot(k - 1) * n : nullptr;
+      rho = st->rho[a];
+    }
+  }
+  twoloop_body(v, upd, part_in, nin, rho, second ? nullptr : alpha_base + a, second, alpha_base + a, nxt, part_out,
+               n, sh);
+}
+
+__global__ void k_dot3_hist(const double *__restrict__ ys, const double *__restrict__ ss, int64_t n,
+                            const LoopState *__restrict__ st, double *__restrict__ part) {
+  __shared__ double sh[NT];
+  const int64_t off = (int64_t)st->head * n;
+  const double *x = ys + off, *y = ss + off;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT) {
+    double xv = x[k], yv = y[k];
+    a = __fma_rn(xv, yv, a);
+    b = __fma_rn(xv, xv, b);
+    c = __fma_rn(yv, yv, c);
+  }
+  a = block_sum<NT>(a, sh);
+  b = block_sum<NT>(b, sh);
+  c = block_sum<NT>(c, sh);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
+  }
+}
+
+// z = 1 x + alpha y, y += alpha x, slot(head) of base = 1 x + (-1) y: the
+// host path's k_lincomb / k_axpy arithmetic with the scalar read on the device
+__global__ void k_lincomb_alpha(double *z, const double *x, const double *y, int64_t n,
+                                const LoopState *__restrict__ st) {
+  const double b = st->alpha;
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT)
+    z[k] = __fma_rn(b, y[k], __dmul_rn(1.0, x[k]));
+}
+__global__ void k_axpy_alpha(double *__restrict__ y, const double *__restrict__ x, int64_t n,
+                             const LoopState *__restrict__ st) {
+  const double a = st->alpha;
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT)
+    y[k] = __fma_rn(a, x[k], y[k]);
+}
+__global__ void k_hist_diff(double *base, const double *x, const double *y, int64_t n,
+                            const LoopState *__restrict__ st) {
+  double *z = base + (int64_t)st->head * n;
+  for (int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x; k < n; k += (int64_t)gridDim.x * NT)
+    z[k] = __fma_rn(-1.0, y[k], __dmul_rn(1.0, x[k]));
 }
 
 __global__ void k_count_free(const uint8_t *__restrict__ fixed, int64_t n, int *__restrict__ out) {
@@ -184,6 +277,57 @@ void two_loop_second(Scene &s, double *r, int64_t n) {
     HOT_LAUNCH("k_twoloop_step");
     std::swap(pa, pb);
   }
+}
+
+void two_loop_first_dev(Scene &s, double *q, int64_t n, const LoopState *st) {
+  const int G = grid_for(s), w = s.opts.lbfgs_m;
+  double *pa = s.part.p, *pb = s.part.p + 2048;
+  k_twoloop_dev<<<G, NT, 0, s.st>>>(q, nullptr, s.hist_s.p, n, w, st, -1, 0, nullptr, 0, pa, s.scal.p);
+  HOT_LAUNCH("k_twoloop_dev");
+  for (int j = 0; j < w; ++j) {
+    k_twoloop_dev<<<G, NT, 0, s.st>>>(q, s.hist_y.p, s.hist_s.p, n, w, st, j, 0, pa, G, pb, s.scal.p);
+    HOT_LAUNCH("k_twoloop_dev");
+    std::swap(pa, pb);
+  }
+}
+
+void two_loop_second_dev(Scene &s, double *r, int64_t n, const LoopState *st) {
+  const int G = grid_for(s), w = s.opts.lbfgs_m;
+  double *pa = s.part.p, *pb = s.part.p + 2048;
+  k_twoloop_dev<<<G, NT, 0, s.st>>>(r, nullptr, s.hist_y.p, n, w, st, -1, 1, nullptr, 0, pa, s.scal.p);
+  HOT_LAUNCH("k_twoloop_dev");
+  for (int j = 0; j < w; ++j) {
+    k_twoloop_dev<<<G, NT, 0, s.st>>>(r, s.hist_s.p, s.hist_y.p, n, w, st, j, 1, pa, G, pb, s.scal.p);
+    HOT_LAUNCH("k_twoloop_dev");
+    std::swap(pa, pb);
+  }
+}
+
+int dot_launch(Scene &s, const double *x, const double *y, int64_t n, int mode, double *part) {
+  const int G = grid_for(s);
+  k_dot3<<<G, NT, 0, s.st>>>(x, y, n, mode, part);
+  HOT_LAUNCH("k_dot3");
+  return G;
+}
+
+int dots3_hist_launch(Scene &s, int64_t n, const LoopState *st, double *part) {
+  const int G = grid_for(s);
+  k_dot3_hist<<<G, NT, 0, s.st>>>(s.hist_y.p, s.hist_s.p, n, st, part);
+  HOT_LAUNCH("k_dot3_hist");
+  return G;
+}
+
+void lincomb_alpha(Scene &s, double *z, const double *x, const double *y, int64_t n, const LoopState *st) {
+  k_lincomb_alpha<<<grid_for(s), NT, 0, s.st>>>(z, x, y, n, st);
+  HOT_LAUNCH("k_lincomb_alpha");
+}
+void axpy_alpha(Scene &s, double *y, const double *x, int64_t n, const LoopState *st) {
+  k_axpy_alpha<<<grid_for(s), NT, 0, s.st>>>(y, x, n, st);
+  HOT_LAUNCH("k_axpy_alpha");
+}
+void hist_diff(Scene &s, double *base, const double *x, const double *y, int64_t n, const LoopState *st) {
+  k_hist_diff<<<grid_for(s), NT, 0, s.st>>>(base, x, y, n, st);
+  HOT_LAUNCH("k_hist_diff");
 }
 
 }  // namespace hot

@@ -69,7 +69,7 @@ class mpm_step_stats(C.Structure):
                 ("vcycles", C.c_int32), ("final_norm", C.c_double), ("energy", C.c_double),
                 ("dt_used", C.c_double), ("n_particles", C.c_int64), ("n_nodes", C.c_int64 * 8),
                 ("nnz_blocks", C.c_int64 * 8), ("n_levels", C.c_int32), ("status", C.c_int32),
-                ("graph_vcycles", C.c_int32), ("reserved", C.c_int32)]
+                ("graph_vcycles", C.c_int32), ("device_loop", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -191,7 +191,8 @@ def stats_dict(s: mpm_step_stats) -> dict:
             "vcycles": s.vcycles, "final_norm": s.final_norm, "energy": s.energy, "dt": s.dt_used,
             "n_particles": s.n_particles, "n_nodes": list(s.n_nodes[:nl]),
             "nnz_blocks": list(s.nnz_blocks[:nl]), "n_levels": nl, "status": s.status,
-            "status_name": STATUS.get(s.status, str(s.status)), "graph_vcycles": s.graph_vcycles}
+            "status_name": STATUS.get(s.status, str(s.status)), "graph_vcycles": s.graph_vcycles,
+            "device_loop": s.device_loop}
 
 
 class HotScene:

@@ -102,7 +102,8 @@ class SolverOptions:
     fps: float = 24.0
     cfl: float = 0.6
     flags: int = 0            # bit 0: V-cycle launched eagerly (no CUDA graph); 1: cooperative
-                              # coarsest PCG; 2: one launch per SGS color; 3: the same, finest level
+                              # coarsest PCG; 2: one launch per SGS color; 3: the same, finest level;
+                              # 4: host-driven L-BFGS loop instead of the device-side graph
 
 
 def _jittered_block(rng, cell_lo, cell_hi, dx, origin, ppc_axis=2):

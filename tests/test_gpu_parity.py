@@ -156,6 +156,29 @@ def test_vcycle_smoothing_launch_modes(hot, flags):
     g.close()
 
 
+@pytest.mark.parametrize("name", ["bars_nh_cn", "cube8k_fcr", "cube_von_mises"])
+def test_device_loop_matches_host_loop(hot, name):
+    """The L-BFGS iterations as one CUDA graph with device-side decisions take
+    the same decisions as the host-driven loop and reach the same iterate
+    (P2G and gradient scatters use FP64 atomics, so sums agree to rounding)."""
+    sc, opts = SCENES[name]
+    runs = {}
+    for flags in (0, 16):
+        g = hot.HotScene(sc, scenes.SolverOptions(**{**opts.__dict__, "flags": flags}))
+        g.p2g()
+        st = g.solve()
+        runs[flags] = (st, g.trace(), g.grid()["dv"])
+        g.close()
+    (sd, td, dd), (sh, th, dh) = runs[0], runs[16]
+    assert sd["device_loop"] == 1 and sh["device_loop"] == 0
+    assert sd["status"] == sh["status"] == 0
+    assert sd["iters"] == sh["iters"] and sd["ls_trials"] == sh["ls_trials"]
+    for k in ("alphas", "ls_trials", "skipped", "fallback", "cg_counts"):
+        assert np.array_equal(np.asarray(td[k]), np.asarray(th[k])), k
+    assert sd["graph_vcycles"] == sd["vcycles"]
+    assert rel(dd, dh) < 1e-12
+
+
 def replay_trace(tr):
     return O.Trace(iters=tr["iters"], alphas=tr["alphas"], ls_trials=tr["ls_trials"],
                    cg_counts=tr["cg_counts"], skipped=tr["skipped"], fallback=tr["fallback"])
