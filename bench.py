@@ -15,6 +15,7 @@ roofline, p50/p99 step latency, and the FP64 oracle on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -153,14 +154,31 @@ def algorithmic_units(name: str, stats_list, n_particles: int, precision: int):
     return 40 * visits, "byte"
 
 
-def roofline_entry(name, prof, stats_list, n_particles, precision, peaks):
+def vcycle_traffic(key):
+    """DRAM bytes per V-cycle (dram__bytes_read.sum + dram__bytes_write.sum
+    over the kernels of one V-cycle) from the committed ncu summary, or None
+    when the V-cycle's source changed after that capture."""
+    try:
+        lines = open(os.path.join(ROOT, "profiles", "vcycle_dram.txt")).read().splitlines()
+        src = open(os.path.join(ROOT, "paper_1911_07913_gb300", "csrc", "multigrid.cu"), "rb").read()
+    except OSError:
+        return None
+    kv = dict(line.split(": ", 1) for line in lines if ": " in line and not line.startswith("#"))
+    if kv.get("multigrid_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    v = kv.get(key)
+    return float(v) if v else None
+
+
+def roofline_entry(name, prof, stats_list, n_particles, precision, peaks, traffic_key=None):
     """Dominant-kernel roofline from live CUDA-event times over the timed steps."""
     p = prof.get(name)
     if not p or p["launches"] == 0:
         return None
     units, kind = algorithmic_units(name, stats_list, n_particles, precision)
     secs = p["ms"] / 1e3
-    base = {"kernel": name, "traffic": None, "launches": p["launches"],
+    traffic = vcycle_traffic(traffic_key) if (traffic_key and name == "vcycle") else None
+    base = {"kernel": name, "traffic": traffic, "traffic_unit": "DRAM bytes per V-cycle (ncu)", "launches": p["launches"],
             "avg_launch_ms": p["ms"] / p["launches"], "algorithmic_total": units, "algorithmic_unit": kind,
             "timed": "CUDA events around every V-cycle, over a replay of the timed steps from their start state"}
     if kind == "flop":
@@ -182,7 +200,7 @@ def load_peaks():
 
 
 # --------------------------------------------------------------------------- our arm
-def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, rank, local, sample_clocks=True):
+def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, rank, local, sample_clocks=True, profile_run=False):
     """Warm-up, one profiled breakdown step, K timed steps (the L-BFGS loop as
     one device-driven CUDA graph, no profiling), then the same K steps replayed
     from the same state with CUDA events around every V-cycle (`dominant`) for
@@ -195,7 +213,7 @@ def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, rank, local, sample_clo
     for _ in range(warmup):
         g.step(check=False)
     breakdown = {}
-    if warmup > 0:
+    if warmup > 0 and not profile_run:
         # full kernel breakdown on one extra untimed step
         g.profile(True)
         g.step()
@@ -220,12 +238,14 @@ def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, rank, local, sample_clo
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     total_ms = ev[0].elapsed_time(ev[steps])
     # roofline: the same steps again, every V-cycle between CUDA events
-    replay_state(g, sc, start_state)
-    g.profile(True, only=dominant)
-    prof_stats = [g.step(check=False) for _ in range(steps)]
-    torch.cuda.synchronize()
-    prof = g.profile_read()
-    g.profile(False)
+    prof, prof_stats = {}, []
+    if not profile_run:
+        replay_state(g, sc, start_state)
+        g.profile(True, only=dominant)
+        prof_stats = [g.step(check=False) for _ in range(steps)]
+        torch.cuda.synchronize()
+        prof = g.profile_read()
+        g.profile(False)
     e2e = None
     if with_e2e:
         e2e = run_e2e(g, sc, steps, stream, start_state)
@@ -429,7 +449,8 @@ def main():
     ap.add_argument("--serve-scenes", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--profile-run", action="store_true",
-                    help="profiling run under ncu: only the timed steps of one workload, warm-up allowed below 3")
+                    help="profiling run under ncu: warm-up and timed steps of one workload only (no breakdown, "
+                         "no roofline replay), warm-up allowed below 3")
     args = ap.parse_args()
     if args.small:
         args.workload = "cube8k"
@@ -457,11 +478,12 @@ def main():
     peaks = load_peaks()
     barrier(ws)
     r = run_gpu(sc, opts, args.steps, args.warmup, args.dominant, not args.no_e2e, rank, local,
-                sample_clocks=not args.profile_run)
+                sample_clocks=not args.profile_run, profile_run=args.profile_run)
     barrier(ws)
     t_max = max_over_ranks(r["total_ms"], ws)
     value = sc.n * ws * args.steps / (t_max / 1e3)
-    roof = roofline_entry(args.dominant, r["prof"], r["prof_stats"], sc.n, opts.precision, peaks)
+    roof = roofline_entry(args.dominant, r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
+                          traffic_key=f"{args.workload}_{'fp64' if opts.precision == 0 else 'mixed'}_bytes_per_vcycle")
     mixed = None
     if not args.no_mixed and args.workload == "two_bars_600k" and args.precision == 0:
         sc2 = scenes.two_bars_2m_scene(seed=rank)
@@ -472,7 +494,8 @@ def main():
         mixed = {"value": sc2.n * ws * args.steps / (t2 / 1e3), "unit": UNIT, "ms_per_step": t2 / args.steps,
                  "p50_ms": float(np.percentile(sm, 50)), "p99_ms": float(np.percentile(sm, 99)),
                  "config": workload_desc(sc2, o2), "iters": [s["iters"] for s in r2["stats"]],
-                 "roofline": roofline_entry("vcycle", r2["prof"], r2["prof_stats"], sc2.n, 1, peaks),
+                 "roofline": roofline_entry("vcycle", r2["prof"], r2["prof_stats"], sc2.n, 1, peaks,
+                                            traffic_key="two_bars_2m_mixed_bytes_per_vcycle"),
                  "kernel_ms": {k: round(v["ms"], 3) for k, v in r2["breakdown"].items()},
                  "clocks": r2["clocks"]}
     batching = serving = None

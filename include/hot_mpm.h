@@ -117,9 +117,12 @@ typedef struct {
                             bit 1: coarsest solve by the cooperative kernel, not the cluster one;
                             bit 2: one launch per Gauss-Seidel color on every level;
                             bit 3: one launch per color on the finest level only;
-                            bit 4: drive the L-BFGS iterations from the host (by default they
-                            run as one CUDA graph whose conditional nodes take every decision
-                            on the device; profiling and bit 0 also select the host loop)
+                            bit 4: drive the L-BFGS iterations from the host;
+                            bit 5: run them as one CUDA graph whose conditional nodes take every
+                            decision on the device (by default the graph is used once the
+                            scene's previous solve took 8 or more iterations: building it costs
+                            about as much as a few host-driven iterations; profiling and bit 0
+                            select the host loop)
                             (by default each symmetric sweep of each level is one
                             cooperative launch); bits 2 and 3 change launch
                             boundaries only, not the arithmetic */
@@ -241,9 +244,11 @@ int64_t mpm_kernel_launch_count(void);
 /* Device bytes held by the scene (its admission footprint). */
 mpm_status mpm_scene_footprint(mpm_scene_t s, int64_t *bytes);
 
-/* Batched stepping: p2g, solve and g2p of n independent scenes.  Scenes on
- * the same stream run back to back; scenes on different streams overlap.
- * stats may be NULL, else n entries. */
+/* Batched stepping: p2g, solve and g2p of n independent scenes, taken from
+ * a shared queue by one worker thread per host core (at most n).  Scenes on
+ * different streams overlap on the GPU; scenes that share a stream are
+ * serialised by it.  stats may be NULL, else n entries.  Returns the first
+ * failing scene's status (mpm_last_error(NULL) names the scene). */
 mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats);
 
 /* Continuous-batching step server (serving many resident scenes).  Requests

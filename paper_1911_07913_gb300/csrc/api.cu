@@ -357,6 +357,7 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   out.status = status;
   out.graph_vcycles = s.graph_launches;
   out.device_loop = on_device ? 1 : 0;
+  s.last_iters = it;
   s.last_stats = out;
   if (st) *st = out;
   return status;
@@ -605,14 +606,20 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
     return MPM_ERR_INVALID_ARG;
   }
   std::vector<mpm_status> res(n, MPM_OK);
+  // one worker per host core at most: a step blocks its thread in stream
+  // synchronisations, and more threads than cores only spin against each other
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int workers = std::max(1, std::min<int>(n, hc ? (int)hc : 8));
+  std::atomic<int> next{0};
   std::vector<std::thread> th;
-  th.reserve(n);
+  th.reserve(workers);
   int dev = 0;
   cudaGetDevice(&dev);
-  for (int i = 0; i < n; ++i)
-    th.emplace_back([&, i]() {
+  for (int k = 0; k < workers; ++k)
+    th.emplace_back([&]() {
       cudaSetDevice(dev);
-      res[i] = mpm_step(scenes[i], stats ? &stats[i] : nullptr);
+      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1))
+        res[i] = mpm_step(scenes[i], stats ? &stats[i] : nullptr);
     });
   for (auto &t : th) t.join();
   for (int i = 0; i < n; ++i)

@@ -7,6 +7,7 @@ namespace hot {
 
 constexpr int MAX_LEVELS = 8;
 constexpr int MAX_HIST = 16;
+constexpr int DEVICE_LOOP_MIN_ITERS = 8;
 constexpr int NSLOT = 125;       // 5^3 block offsets per row (Sec. 6 "Sparse matrix storage")
 constexpr int DIAG_SLOT = 62;    // offset (0,0,0)
 
@@ -181,6 +182,7 @@ struct Scene {
   DBuf<int> tr_int;            // ... line-search trials | skipped pairs | fallbacks
   cudaStream_t aux_st[2] = {nullptr, nullptr};   // streams for captures of conditional bodies
   bool loop_graph_ok = true;
+  int last_iters = -1;             // L-BFGS iterations of the previous solve
 
   int nlev = 0;
   Topo topo[MAX_LEVELS];

@@ -200,6 +200,10 @@ struct Counts {
 bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double &E, double &nrm, int &it,
                       int &trials_total, mpm_status &status) {
   if (!s.loop_graph_ok || !s.graphs_ok || s.prof || (s.opts.flags & 17) || s.nn() == 0) return false;
+  // building the graph costs about as much host time as a handful of host-
+  // driven iterations: by default it is used once the scene's previous solve
+  // took at least DEVICE_LOOP_MIN_ITERS iterations (bit 5 forces it)
+  if (!(s.opts.flags & 32) && s.last_iters < DEVICE_LOOP_MIN_ITERS) return false;
   const int64_t n3 = 3 * s.nn();
   const int w = s.opts.lbfgs_m, cap = s.opts.max_iters + 1, max_ls = s.opts.max_ls;
   const int cn = s.opts.cn_mode, max_iters = s.opts.max_iters;

@@ -103,7 +103,7 @@ class SolverOptions:
     cfl: float = 0.6
     flags: int = 0            # bit 0: V-cycle launched eagerly (no CUDA graph); 1: cooperative
                               # coarsest PCG; 2: one launch per SGS color; 3: the same, finest level;
-                              # 4: host-driven L-BFGS loop instead of the device-side graph
+                              # 4: host-driven L-BFGS loop; 5: device-side graph loop always
 
 
 def _jittered_block(rng, cell_lo, cell_hi, dx, origin, ppc_axis=2):
