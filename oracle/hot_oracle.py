@@ -20,6 +20,10 @@ Integration for CFL-rate MPM Stepping" (HOT), in numpy/scipy float64:
 * Alg. 3 HOT: L-BFGS (window w) with the V-cycle as initial inverse Hessian,
   backtracking line search, node-wise characteristic-norm termination
   (Sec. 5.2, Eq. "nodewiseCN").
+* Alg. 1 inexact projected Newton, the paper's comparison solvers: PN-PCG
+  (Jacobi-preconditioned CG) and PN-MGPCG (one V-cycle of a hierarchy
+  rebuilt every Newton iteration as the preconditioner, Sec. 4.3), both with
+  the inexact criterion of Sec. 5.3.
 
 Readings of silent or garbled passages are marked READING and listed in the
 design notes; every function says which passage it follows.  Library
@@ -742,6 +746,124 @@ def hot_solve(prob: Problem, opts, replay: Optional[Trace] = None, levels=None):
         it += 1
     tr.iters = it
     tr.cg_counts = list(vc.cg_counts)
+    return dv, tr
+
+
+# --------------------------------------------------------------------------
+# Alg. 1: inexact projected Newton (PN-PCG, PN-MGPCG)
+# --------------------------------------------------------------------------
+def pn_pcg(H, b, precond, tau, max_iter, forced_iters=None):
+    """CG on H x = b from x = 0 with preconditioner z = precond(r), stopped by
+    the inexact criterion of Sec. 5.3: k = min(0.5, sqrt(max(sqrt(r0^T P r0),
+    tau))) and stop when sqrt(r^T P r) <= k sqrt(r0^T P r0), P the
+    preconditioner (r^T P r = r^T z).  READING: the run is capped at
+    max_iter iterations (the paper states no cap).  Returns (x, iterations)."""
+    bf = b.ravel()
+    x = np.zeros_like(bf)
+    r = bf.copy()
+    z = precond(r)
+    p = z.copy()
+    rz = float(r @ z)
+    bn = np.sqrt(max(rz, 0.0))
+    k = min(0.5, np.sqrt(max(bn, tau)))
+    it = 0
+    while True:
+        if forced_iters is not None:
+            if it >= forced_iters:
+                break
+        elif np.sqrt(max(rz, 0.0)) <= k * bn or it >= max_iter:
+            break
+        Ap = H @ p
+        pAp = float(p @ Ap)
+        if pAp <= 0:
+            break
+        alpha = rz / pAp
+        x += alpha * p
+        r -= alpha * Ap
+        z = precond(r)
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        p = z + beta * p
+        rz = rz_new
+        it += 1
+    return x.reshape(b.shape), it
+
+
+@dataclasses.dataclass
+class PNTrace:
+    iters: int = 0
+    alphas: List[float] = dataclasses.field(default_factory=list)
+    ls_trials: List[int] = dataclasses.field(default_factory=list)
+    cg_iters: List[int] = dataclasses.field(default_factory=list)      # per Newton iteration
+    vc_cg_counts: List[int] = dataclasses.field(default_factory=list)  # coarsest PCG, per V-cycle (PN-MGPCG)
+    energies: List[float] = dataclasses.field(default_factory=list)
+    norms: List[float] = dataclasses.field(default_factory=list)
+    status: str = "ok"
+
+
+def pn_solve(prob: Problem, opts, precond: str = "jacobi", max_cg: int = 10000,
+             replay: Optional[PNTrace] = None):
+    """Alg. 1: Newton iterations on E(dv), each solving the projected Hessian
+    system H p = -g at the current dv (Teran projection, Dirichlet projection)
+    inexactly by PCG (pn_pcg), then the backtracking line search from alpha =
+    1 and the same termination test as Alg. 3.  precond "jacobi": the scalar
+    diagonal of H (PN-PCG); "mg": one V-cycle (Alg. 2, same coarsest solve)
+    of the Galerkin hierarchy built from that H (PN-MGPCG).  With ``replay``
+    the CG iteration counts (and coarsest-PCG counts) and step lengths of
+    another implementation are imposed.  Returns (dv, trace)."""
+    n = prob.n
+    dv = np.zeros((n, 3))
+    g = prob.gradient(dv)
+    g1n = float(np.sqrt(np.sum(g * g)))
+    E = prob.energy(dv)
+    tr = PNTrace()
+    tr.energies.append(E)
+    pattern = prob.hessian_pattern() if precond == "mg" else None
+    vc_forced = list(replay.vc_cg_counts) if replay is not None else None
+    it = 0
+    while True:
+        if opts.cn_mode == 0:
+            nrm, nfree = prob.cn_norm(g)
+            done = nrm <= opts.eps * np.sqrt(nfree)
+        else:
+            nrm = float(np.sqrt(np.sum(g * g)))
+            done = nrm <= opts.eps * g1n
+        tr.norms.append(nrm)
+        if replay is not None:
+            done = it >= replay.iters
+        if done:
+            break
+        if it >= opts.max_iters:
+            tr.status = "not_converged"
+            break
+        H = prob.hessian(dv)
+        if precond == "jacobi":
+            d = H.diagonal()
+            M = lambda r: r / d  # noqa: E731
+        else:
+            levels = build_hierarchy(prob.g.coords, H, pattern, opts.levels)
+            vc = VCycle(levels, prob.g.fixed, opts.eps, opts.max_coarse_cg)
+            if vc_forced is not None:
+                vc.forced = vc_forced           # shared: consumed across Newton iterations
+            M = lambda r: vc(r.reshape(-1, 3)).ravel()  # noqa: E731
+        forced = replay.cg_iters[it] if replay is not None else None
+        p, its = pn_pcg(H, -g, M, opts.eps, max_cg, forced)
+        tr.cg_iters.append(its)
+        if precond == "mg":
+            tr.vc_cg_counts.extend(vc.cg_counts)
+        fa = replay.alphas[it] if replay is not None else None
+        alpha, E1, trials = line_search(prob, dv, p, E, opts.max_ls, fa)
+        if alpha is None:
+            tr.status = "linesearch"
+            break
+        tr.alphas.append(alpha)
+        tr.ls_trials.append(trials if trials is not None else replay.ls_trials[it])
+        dv = dv + alpha * p
+        g = prob.gradient(dv)
+        E = E1
+        tr.energies.append(E)
+        it += 1
+    tr.iters = it
     return dv, tr
 
 

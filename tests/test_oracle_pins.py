@@ -563,3 +563,60 @@ def test_snow_clamp():
     assert np.array_equal(O.plasticity(inside, np.ones(1), np.full(1, 2), np.zeros(1)), inside)
     Q = rand_rot(rng, n)
     np.testing.assert_allclose(O.plasticity(Q @ F, np.ones(n), np.full(n, 2), np.zeros(n)), Q @ out, atol=1e-13)
+
+
+# ------------------------------------------------- Alg. 1: inexact projected Newton
+def test_pn_pcg_is_conjugate_gradients_with_the_inexact_stop():
+    """pn_pcg run to n iterations is CG: it solves an SPD system exactly (up
+    to rounding), and its own stop is the first iterate whose residual,
+    recomputed as b - H x, meets sqrt(r^T P r) <= k sqrt(b^T P b) with
+    k = min(0.5, sqrt(max(sqrt(b^T P b), tau))) (Sec. 5.3)."""
+    rng = np.random.default_rng(11)
+    n = 24
+    Q = rng.normal(size=(n, n))
+    H = sp.csr_matrix(Q @ Q.T + n * np.diag(rng.uniform(0.5, 4.0, n)))
+    b = rng.normal(size=n) * 1e-3
+    d = H.diagonal()
+    jac = lambda r: r / d  # noqa: E731
+    x, its = O.pn_pcg(H, b, jac, 1e-30, 1000, forced_iters=n)
+    np.testing.assert_allclose(x, np.linalg.solve(H.toarray(), b), rtol=1e-9, atol=1e-15)
+    x, its = O.pn_pcg(H, b, jac, 1e-30, 1000)
+    bPb = float(b @ (b / d))
+    k = min(0.5, np.sqrt(max(np.sqrt(bPb), 1e-30)))
+    def enorm(xx):
+        r = b - H @ xx
+        return np.sqrt(float(r @ (r / d)))
+    assert its >= 1 and enorm(x) <= k * np.sqrt(bPb) * (1 + 1e-9)
+    xp, _ = O.pn_pcg(H, b, jac, 1e-30, 1000, forced_iters=its - 1)
+    assert enorm(xp) > k * np.sqrt(bPb)
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "mg"])
+def test_pn_solvers_match_dense_newton_on_tiny_grid(precond):
+    sc = scenes.tiny_scene(seed=3, res=16, cells=(1, 1, 1), lo=(6, 6, 6), ppc_axis=2,
+                           model=1, E=1e4, F_jitter=0.1)
+    g = O.p2g(sc)
+    prob = O.Problem(sc, g, 2e-2)
+    opts = scenes.SolverOptions(eps=1e-8, cn_mode=1, levels=2, max_iters=200)
+    dv, tr = O.pn_solve(prob, opts, precond)
+    assert tr.status == "ok" and tr.iters >= 1
+    ref = dense_newton(prob)
+    np.testing.assert_allclose(dv, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+    assert np.all(np.diff(tr.energies) <= 0)
+    assert all(c >= 1 for c in tr.cg_iters)
+    if precond == "mg":
+        assert len(tr.vc_cg_counts) >= sum(tr.cg_iters)   # one V-cycle per CG iteration (+ the initial one)
+
+
+def test_pn_replay_reproduces_solve_and_agrees_with_hot():
+    sc = scenes.cube_scene(seed=2, res=16, cube_lo=(5, 4, 5), side=4)
+    opts = scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=4e-3, levels=2)
+    grid = O.p2g(sc)
+    prob = O.Problem(sc, grid, O.step_dt(sc, opts))
+    for pc in ("jacobi", "mg"):
+        dv, tr = O.pn_solve(prob, opts, pc)
+        dv2, tr2 = O.pn_solve(prob, opts, pc, replay=tr)
+        np.testing.assert_array_equal(dv2, dv)
+    # all three solvers stop at the same tolerance on the same problem
+    dvh, trh = O.hot_solve(prob, opts)
+    assert np.abs(dv - dvh).max() <= 1e-4 * np.abs(dvh).max()
