@@ -116,21 +116,29 @@ typedef struct {
   int32_t flags;         /* bit 0: run the V-cycle eagerly instead of as a CUDA graph;
                             bit 1: coarsest solve by the cooperative kernel, not the cluster one;
                             bit 2: one launch per Gauss-Seidel color on every level;
-                            bit 3: one launch per color on the finest level only;
+                            bit 3: one launch per color on the finest level only (by default
+                            each symmetric sweep of each level is one cooperative launch;
+                            bits 2 and 3 change launch boundaries only, not the arithmetic);
                             bit 4: drive the L-BFGS iterations from the host;
                             bit 5: run them as one CUDA graph whose conditional nodes take every
                             decision on the device (by default the graph is used once the
                             scene's previous solve took 8 or more iterations: building it costs
                             about as much as a few host-driven iterations; profiling and bit 0
-                            select the host loop)
-                            (by default each symmetric sweep of each level is one
-                            cooperative launch); bits 2 and 3 change launch
-                            boundaries only, not the arithmetic */
-  int32_t reserved;
+                            select the host loop) */
+  int32_t solver;        /* 0: HOT (Alg. 3); the paper's comparison solvers, Alg. 1 inexact
+                            projected Newton with the Sec. 5.3 criterion and the Hessian
+                            rebuilt at every Newton iterate: 1: PN-PCG (Jacobi-preconditioned
+                            CG), 2: PN-MGPCG (CG preconditioned by one V-cycle of a hierarchy
+                            rebuilt every Newton iteration, Sec. 4.3).  For 1 and 2, max_iters
+                            caps the Newton iterations and each CG run is capped at
+                            MPM_PN_MAX_CG iterations. */
 } mpm_solver_opts;
 
+#define MPM_PN_MAX_CG 10000
+
 typedef struct {
-  int32_t iters;           /* L-BFGS iterations (Alg. 3 loop trips) */
+  int32_t iters;           /* L-BFGS iterations (Alg. 3 loop trips); Newton iterations for the
+                              projected-Newton solvers */
   int32_t ls_trials;       /* energy evaluations in line searches */
   int32_t coarse_cg_iters; /* coarsest PCG iterations over all V-cycles */
   int32_t vcycles;
@@ -227,6 +235,11 @@ mpm_status mpm_apply_vcycle(mpm_scene_t s, const double *b, double *u, int32_t *
 mpm_status mpm_get_trace(mpm_scene_t s, int32_t capacity, int32_t *n_iters, double *alphas,
                          int32_t *ls_trials, int32_t *skipped, int32_t *fallback,
                          int32_t *n_vcycles, int32_t *cg_counts);
+
+/* Projected-Newton solvers (solver = 1, 2): CG iterations of each Newton
+ * iteration of the last solve.  *n receives the Newton iteration count
+ * (entries beyond capacity are not written). */
+mpm_status mpm_get_inner_iters(mpm_scene_t s, int32_t capacity, int32_t *n, int32_t *cg_iters);
 
 /* Per-kernel device timing.  mpm_profile(s, 1, only) clears and starts
  * recording CUDA events on the scene's stream around the library's main

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhotmpm.so")
-SOURCES = ["api.cu", "transfer.cu", "elastic.cu", "multigrid.cu", "vecops.cu", "scan.cu", "noalloc.cu", "server.cu", "solve_graph.cu"]
+SOURCES = ["api.cu", "transfer.cu", "elastic.cu", "multigrid.cu", "vecops.cu", "scan.cu", "noalloc.cu", "server.cu", "solve_graph.cu", "newton.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

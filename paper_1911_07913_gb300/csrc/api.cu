@@ -46,6 +46,9 @@ static cudaEvent_t take_event(Scene &s) {
 
 ProfScope::ProfScope(Scene &sc, const char *name) : s(&sc), id(-1) {
   if (!sc.prof) return;
+  // no events inside a stream capture (conditional graph bodies refuse them)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(sc.st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   if (!sc.prof_only.empty() && sc.prof_only != name) return;
   for (size_t k = 0; k < sc.prof_names.size(); ++k)
     if (sc.prof_names[k] == name) id = (int)k;
@@ -107,7 +110,8 @@ size_t Scene::bytes() const {
              v.bytes() + xi.bytes() + fixed.bytes() + mv.bytes() + mxi.bytes() + dv.bytes() + g.bytes() +
              pdir.bytes() + q.bytes() + g_new.bytes() + dv_new.bytes() + vtmp.bytes() + hist_s.bytes() +
              hist_y.bytes() + Lv.bytes() + Lp.bytes() + Le.bytes() + dv_e.bytes() + g_e.bytes() + gscr.bytes() +
-             part.bytes() + tr_alpha.bytes() + tr_int.bytes() + lstate.bytes() +
+             part.bytes() + tr_alpha.bytes() + tr_int.bytes() + lstate.bytes() + cg_r.bytes() + cg_z.bytes() +
+             cg_p.bytes() + cg_Ap.bytes() + cgs.bytes() +
              scal.bytes() + errflag.bytes() + scan.block_sums.bytes() + scan.total.bytes() + hd.bytes() + hf.bytes();
   for (auto &t : topo) b += t.bytes();
   return b;
@@ -118,6 +122,8 @@ void Scene::release() {
                   &hist_y, &Lv, &Lp, &part, &scal, &Le, &dv_e, &g_e, &gscr, &tr_alpha})
     b->release();
   lstate.release();
+  for (auto *b : {&cg_r, &cg_z, &cg_p, &cg_Ap}) b->release();
+  cgs.release();
   for (auto *b : {&pmat, &pmat_alt, &pid, &pid_alt, &slot, &perm, &tmp, &cell_count, &cell_start, &cell_first,
                   &cell_n, &cell_key, &blk_first, &blk_end, &blk_key, &flags, &flag_scan, &errflag, &tr_int})
     b->release();
@@ -147,6 +153,7 @@ void validate_opts(const mpm_solver_opts *o) {
   if (o->precision != 0 && o->precision != 1) fail(MPM_ERR_INVALID_ARG, "precision must be 0 or 1");
   if (o->max_iters < 1 || o->max_ls < 1) fail(MPM_ERR_INVALID_ARG, "max_iters and max_ls must be >= 1");
   if (o->max_coarse_cg < 0) fail(MPM_ERR_INVALID_ARG, "max_coarse_cg must be >= 0");
+  if (o->solver < 0 || o->solver > 2) fail(MPM_ERR_INVALID_ARG, "solver must be 0 (HOT), 1 (PN-PCG) or 2 (PN-MGPCG)");
   if (o->dt <= 0.0 && !(o->fps > 0.0 && o->cfl > 0.0)) fail(MPM_ERR_INVALID_ARG, "need dt > 0 or fps, cfl > 0");
 }
 
@@ -192,7 +199,8 @@ void build_hier(Scene &s, Hier<T> &h) {
   hessian_assemble<T>(s, h);
   finalize_values<T>(s, h, 0);
   int M = 1;
-  for (int m = 0; m + 1 < s.opts.levels; ++m) {
+  const int levels = s.opts.solver == 1 ? 1 : s.opts.levels;   // PN-PCG needs the fine matrix only
+  for (int m = 0; m + 1 < levels; ++m) {
     build_coarse_topology(s, m);
     build_colors(s, m + 1);
     rap<T>(s, h, m);
@@ -223,6 +231,58 @@ std::vector<int> read_log(Scene &s) {
   return s.opts.precision == 0 ? read_cg_log<double>(s, s.hd) : read_cg_log<float>(s, s.hf);
 }
 
+// Alg. 1 (the comparison solvers): Newton iterations with the projected
+// Hessian rebuilt at every iterate, the inexact CG solve (newton.cu), the
+// same backtracking line search and termination test as the L-BFGS loop.
+void pn_loop(Scene &s, double &E, double norms[2], double thr, double &nrm, int &it, int &trials_total,
+             int &inner_total, mpm_status &status) {
+  const int64_t n3 = 3 * s.nn();
+  if (s.nn() == 0) return;
+  pn_prepare(s);
+  while (true) {
+    if (!std::isfinite(norms[0]) || !std::isfinite(norms[1]) || !std::isfinite(E)) {
+      status = MPM_ERR_NUMERIC;
+      break;
+    }
+    nrm = std::sqrt(s.opts.cn_mode == 0 ? norms[1] : norms[0]);
+    if (nrm <= thr) break;
+    if (it >= s.opts.max_iters) {
+      status = MPM_ERR_NOT_CONVERGED;
+      break;
+    }
+    if (it > 0) pn_rebuild_values(s);   // the hierarchy built for this step is the one at dv = 0
+    const int cg = pn_cg_run(s);        // s.pdir <- p, H p ~ -g
+    s.trace.inner.push_back(cg);
+    inner_total += cg;
+    velocity_gradient(s, s.pdir.p, nullptr, s.Lp.p);
+    double alpha = 1.0, E1 = E;
+    int t = 0;
+    bool ok = false;
+    for (t = 1; t <= s.opts.max_ls; ++t) {
+      E1 = energy(s, s.Lv.p, s.Lp.p, alpha, s.dv.p, s.pdir.p);
+      if (E1 <= E) {
+        ok = true;
+        break;
+      }
+      alpha *= 0.5;
+    }
+    trials_total += ok ? t : s.opts.max_ls;
+    if (!ok) {
+      status = MPM_ERR_LINESEARCH;
+      break;
+    }
+    s.trace.alphas.push_back(alpha);
+    s.trace.ls_trials.push_back(t);
+    lincomb(s, s.dv_new.p, 1.0, s.dv.p, alpha, s.pdir.p, n3);
+    axpy(s, s.Lv.p, alpha, s.Lp.p, 9 * s.np);
+    std::swap(s.dv, s.dv_new);
+    gradient(s, s.Lv.p, s.dv.p, s.g.p, norms);
+    E = E1;
+    ++it;
+  }
+  pn_release(s);
+}
+
 mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   if (s.phase < PH_P2G) fail(MPM_ERR_STATE, "mpm_p2g must run before mpm_solve_step");
   if (s.phase < PH_HIER) do_build(s);
@@ -247,11 +307,14 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   const double g1n = std::sqrt(norms[0]);
   double E = energy(s, s.Lv.p, nullptr, 0.0, s.dv.p, nullptr);
   mpm_status status = MPM_OK;
-  int it = 0, trials_total = 0, cg_total = 0;
+  int it = 0, trials_total = 0, cg_total = 0, inner_total = 0;
   double nrm = 0.0;
   const double thr = s.opts.cn_mode == 0 ? s.opts.eps * std::sqrt((double)nfree) : s.opts.eps * g1n;
-  const bool on_device = solve_loop_graph(s, E, norms, thr, E, nrm, it, trials_total, status);
-  while (!on_device) {
+  if (s.opts.solver != 0) {
+    pn_loop(s, E, norms, thr, nrm, it, trials_total, inner_total, status);
+  }
+  const bool on_device = s.opts.solver == 0 && solve_loop_graph(s, E, norms, thr, E, nrm, it, trials_total, status);
+  while (s.opts.solver == 0 && !on_device) {
     if (!std::isfinite(norms[0]) || !std::isfinite(norms[1]) || !std::isfinite(E)) {
       status = MPM_ERR_NUMERIC;
       break;
@@ -530,6 +593,7 @@ mpm_status mpm_destroy_scene(mpm_scene_t sc) {
   Scene *s = reinterpret_cast<Scene *>(sc);
   cudaStreamSynchronize(s->st);
   s->drop_graph();
+  pn_release(*s);
   s->release();
   for (auto a : s->aux_st)
     if (a) cudaStreamDestroy(a);
@@ -756,6 +820,19 @@ mpm_status mpm_apply_vcycle(mpm_scene_t sc, const double *b, double *u, int32_t 
     std::vector<int> lg = read_log(*s);
     if (cg_iters) *cg_iters = lg.empty() ? 0 : lg.back();
     if (read_errflag(*s) & DEV_ERR_TIMEOUT) fail(MPM_ERR_TIMEOUT, "coarse solve barrier timed out");
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_get_inner_iters(mpm_scene_t sc, int32_t capacity, int32_t *n, int32_t *cg_iters) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s || !n) fail(MPM_ERR_INVALID_ARG, "NULL argument");
+    const std::vector<int> &v = s->trace.inner;
+    *n = (int32_t)v.size();
+    const int k = std::min<int>(capacity, (int)v.size());
+    for (int i = 0; i < k; ++i)
+      if (cg_iters) cg_iters[i] = v[i];
     return MPM_OK;
   });
 }

@@ -106,10 +106,24 @@ struct Trace {
   int iters = 0;
   std::vector<double> alphas;
   std::vector<int> ls_trials, skipped, fallback, cg_counts;
+  std::vector<int> inner;   // CG iterations per Newton iteration (projected-Newton solvers)
   void clear() {
     iters = 0;
-    alphas.clear(); ls_trials.clear(); skipped.clear(); fallback.clear(); cg_counts.clear();
+    alphas.clear(); ls_trials.clear(); skipped.clear(); fallback.clear(); cg_counts.clear(); inner.clear();
   }
+};
+
+// Scalars of the projected-Newton CG loop, in device memory.
+struct CgState {
+  double rz, bn, k, pAp, alpha, beta;
+  int it, stop;
+};
+
+// The captured CG loop of the projected-Newton solvers (one per solve).
+struct PnGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long top_kernels = 0, body_kernels = 0, upd_kernels = 0;
 };
 
 // Scalars of the device-driven L-BFGS loop (Alg. 3), in device memory.
@@ -178,6 +192,9 @@ struct Scene {
   DBuf<int> errflag;
   ScanScratch scan;
   DBuf<LoopState> lstate;      // device-driven loop scalars
+  DBuf<double> cg_r, cg_z, cg_p, cg_Ap;   // projected-Newton CG vectors (3n)
+  DBuf<CgState> cgs;
+  PnGraph pn_graph;
   DBuf<double> tr_alpha;       // device-driven loop trace: step lengths
   DBuf<int> tr_int;            // ... line-search trials | skipped pairs | fallbacks
   cudaStream_t aux_st[2] = {nullptr, nullptr};   // streams for captures of conditional bodies
@@ -229,6 +246,8 @@ struct Scene {
     key.st = s;
     fixed.st = s;
     lstate.st = s;
+    cgs.st = s;
+    cg_r.st = cg_z.st = cg_p.st = cg_Ap.st = s;
     mat_table.st = s;
     bc_dev.st = s;
     scan.block_sums.st = scan.total.st = s;
@@ -322,6 +341,12 @@ void hist_diff(Scene &s, double *base, const double *x, const double *y, int64_t
 // decisions); returns false, touching nothing, when the graph cannot be built.
 bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double &E, double &nrm, int &it,
                       int &trials_total, mpm_status &status);
+
+// ---- newton.cu (Alg. 1, the comparison solvers)
+void pn_prepare(Scene &s);          // captures the CG loop (buffers, V-cycle plan first)
+int pn_cg_run(Scene &s);            // CG on H p = -g into s.pdir; returns its iterations
+void pn_release(Scene &s);
+void pn_rebuild_values(Scene &s);   // projected Hessian (and hierarchy) at the current s.Lv
 void note_launches(long long n);   // adds to the kernel launch counter
 long long launch_count();
 

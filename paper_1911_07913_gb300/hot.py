@@ -26,7 +26,7 @@ OK, NOT_CONVERGED, LINESEARCH = 0, 4, 5
 EXPORTED = ["mpm_set_allocator", "mpm_create_scene", "mpm_destroy_scene", "mpm_last_error",
             "mpm_set_options", "mpm_p2g", "mpm_build_hierarchy", "mpm_solve_step", "mpm_g2p",
             "mpm_step", "mpm_get_state", "mpm_set_state", "mpm_get_grid", "mpm_eval_energy",
-            "mpm_eval_gradient", "mpm_get_hessian", "mpm_apply_vcycle", "mpm_get_trace",
+            "mpm_eval_gradient", "mpm_get_hessian", "mpm_apply_vcycle", "mpm_get_trace", "mpm_get_inner_iters",
             "mpm_scene_footprint", "mpm_step_batch", "mpm_profile", "mpm_profile_read",
             "mpm_kernel_launch_count", "mpm_particle_energy_noalloc", "mpm_server_create",
             "mpm_server_submit", "mpm_server_poll", "mpm_server_info", "mpm_server_destroy"]
@@ -61,7 +61,7 @@ class mpm_solver_opts(C.Structure):
                 ("levels", C.c_int32), ("precision", C.c_int32), ("max_iters", C.c_int32),
                 ("max_ls", C.c_int32), ("max_coarse_cg", C.c_int32), ("record_trace", C.c_int32),
                 ("dt", C.c_double), ("fps", C.c_double), ("cfl", C.c_double), ("flags", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("solver", C.c_int32)]
 
 
 class mpm_step_stats(C.Structure):
@@ -121,6 +121,7 @@ def load(install_torch_allocator: bool = True):
     lib.mpm_apply_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]
     lib.mpm_get_trace.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]
+    lib.mpm_get_inner_iters.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p]
     lib.mpm_scene_footprint.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
     lib.mpm_step_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(mpm_step_stats)]
     lib.mpm_set_allocator.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -182,7 +183,7 @@ def opts_struct(o: _scenes.SolverOptions) -> mpm_solver_opts:
     return mpm_solver_opts(eps=o.eps, cn_mode=o.cn_mode, lbfgs_m=o.lbfgs_m, levels=o.levels,
                            precision=o.precision, max_iters=o.max_iters, max_ls=o.max_ls,
                            max_coarse_cg=o.max_coarse_cg, record_trace=1, dt=o.dt, fps=o.fps,
-                           cfl=o.cfl, flags=getattr(o, "flags", 0))
+                           cfl=o.cfl, flags=getattr(o, "flags", 0), solver=getattr(o, "solver", 0))
 
 
 def stats_dict(s: mpm_step_stats) -> dict:
@@ -365,6 +366,13 @@ class HotScene:
         return {"iters": k, "alphas": al[:k].tolist(), "ls_trials": ls[:k].tolist(),
                 "skipped": sk[:k].tolist(), "fallback": fb[:k].tolist(),
                 "cg_counts": cg[:nv.value].tolist()}
+
+    def inner_iters(self, capacity: int = 100000) -> list:
+        """CG iterations of each Newton iteration (projected-Newton solvers)."""
+        n = C.c_int32()
+        out = np.zeros(capacity, np.int32)
+        self._check(self.lib.mpm_get_inner_iters(self.h, capacity, C.byref(n), _ptr(out)))
+        return out[:min(n.value, capacity)].tolist()
 
     def profile(self, enable: bool = True, only: Optional[str] = None):
         self._check(self.lib.mpm_profile(self.h, 1 if enable else 0, only.encode() if only else None))

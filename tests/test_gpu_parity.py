@@ -179,6 +179,41 @@ def test_device_loop_matches_host_loop(hot, name):
     assert rel(dd, dh) < 1e-12
 
 
+@pytest.mark.parametrize("solver", [1, 2])
+@pytest.mark.parametrize("name", ["bars_nh_cn", "cube8k_fcr"])
+def test_projected_newton_replay_parity(hot, name, solver):
+    """Alg. 1 (PN-PCG, PN-MGPCG): the oracle, replaying the GPU's CG
+    iteration counts (and coarsest-PCG counts) and step lengths, reaches the
+    same iterate; the GPU's result passes the oracle's own termination test."""
+    sc, opts = SCENES[name]
+    opts = scenes.SolverOptions(**{**opts.__dict__, "solver": solver})
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    st = g.solve()
+    assert st["status"] == 0
+    tr, inner = g.trace(), g.inner_iters()
+    dv = g.grid()["dv"]
+    g.close()
+    assert len(inner) == st["iters"] >= 1 and all(c >= 1 for c in inner)
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, st["dt"])
+    rep = O.PNTrace(iters=st["iters"], alphas=tr["alphas"], ls_trials=tr["ls_trials"], cg_iters=inner,
+                    vc_cg_counts=tr["cg_counts"])
+    dvo, tro = O.pn_solve(prob, opts, "jacobi" if solver == 1 else "mg", replay=rep)
+    # Hundreds of CG iterations per Newton step amplify the rounding of the
+    # inner products (GPU block partials against numpy's sums) by about the
+    # preconditioned condition number, so replayed iterates agree to ~1e-8
+    # here, not to the 1e-9 of the L-BFGS path (which applies one fixed
+    # linear operator per iteration).
+    assert rel(dv, dvo) < 1e-7
+    gr = prob.gradient(dv)
+    if opts.cn_mode == 0:
+        nrm, nfree = prob.cn_norm(gr)
+        assert nrm <= opts.eps * np.sqrt(nfree) * (1 + 1e-6)
+    else:
+        assert np.sqrt(np.sum(gr * gr)) <= opts.eps * np.sqrt(np.sum(prob.gradient(0 * dv) ** 2)) * (1 + 1e-6)
+
+
 def replay_trace(tr):
     return O.Trace(iters=tr["iters"], alphas=tr["alphas"], ls_trials=tr["ls_trials"],
                    cg_counts=tr["cg_counts"], skipped=tr["skipped"], fallback=tr["fallback"])
