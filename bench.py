@@ -293,6 +293,7 @@ def run_batching(seed, steps, count=64):
     opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500)
     gs = [hot.HotScene(sc, opts) for sc in scs]
     hot.step_batch(gs, check=False)       # warm-up: allocations, first hierarchy
+    tuned = hot.batch_autotune(gs, 1)     # launch configuration: 6 more (ordinary) steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     iters = []
@@ -313,19 +314,56 @@ def run_batching(seed, steps, count=64):
     return {"value": n_total * steps / secs, "unit": UNIT, "scenes": count, "particles": n_total,
             "ms_per_batch_step": 1e3 * secs / steps, "sequential_value": n_total / seq,
             "speedup_vs_sequential": (n_total * steps / secs) / (n_total / seq),
+            "autotuned": tuned,
             "lbfgs_iters_per_batch_step": iters,
             "config": "64 boxes, N_p log-uniform 5k-200k, grids 64^3/96^3/128^3, FCR E log-uniform 1e4-1e8, "
                       "half von Mises (yield 1e4 Pa), FP32 preconditioner, 3 levels, CN eps 1e-7, CFL dt"}
 
 
-def run_serving(seed, count=256, requests=512, workers=12, budget_gb=150.0, load=0.8):
+def run_solvers(seed, steps=2, warmup=1):
+    """HOT against the paper's comparison solvers (Alg. 1: PN-PCG, PN-MGPCG)
+    on the two-bar scene at dx = 1/128 (75,200 particles, FP64, CN eps 1e-7,
+    4 levels): wall time per step on the device, same steps from the same
+    state for each solver."""
+    import torch
+    from paper_1911_07913_gb300 import hot
+    sc = scenes.two_bars_scene(seed=seed, res=128, width=10, length=47, gap=4)
+    out = {"workload": f"two bars at dx=1/128, {sc.n} particles, FP64, CN eps 1e-7, 4 levels, {steps} steps "
+                       f"after {warmup} warm-up step(s)"}
+    names = {0: "hot", 1: "pn_pcg", 2: "pn_mgpcg"}
+    for solver in (0, 1, 2):
+        opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=4, precision=0, max_iters=500, solver=solver)
+        stream = torch.cuda.Stream()
+        g = hot.HotScene(sc, opts, stream=stream.cuda_stream)
+        for _ in range(warmup):
+            g.step(check=False)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        its, inner = [], []
+        for _ in range(steps):
+            st = g.step(check=False)
+            its.append(st["iters"])
+            inner.append(int(sum(g.inner_iters())) if solver else 0)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / steps
+        out[names[solver]] = {"ms_per_step": ms, "outer_iters": its, "cg_iters": inner if solver else None}
+        g.close()
+    out["hot_speedup_vs_pn_pcg"] = out["pn_pcg"]["ms_per_step"] / out["hot"]["ms_per_step"]
+    out["hot_speedup_vs_pn_mgpcg"] = out["pn_mgpcg"]["ms_per_step"] / out["hot"]["ms_per_step"]
+    return out
+
+
+def run_serving(seed, count=256, requests=512, workers=12, budget_gb=150.0, load=0.8, flags=0):
     """Resident scenes behind the continuous-batching server: a saturating
     burst measures capacity, then a Poisson stream at `load` of that capacity
-    measures request latency (arrival -> result)."""
+    measures request latency (arrival -> result).  `flags`: the launch
+    configuration the batch autotuner chose for the same kind of workload."""
     import torch
     from paper_1911_07913_gb300 import hot
     scs = scenes.serving_scenes(seed=seed, count=count)
-    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500)
+    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500, flags=flags)
     gs = [hot.HotScene(sc, opts) for sc in scs]
     srv = hot.StepServer(budget_bytes=int(budget_gb * (1 << 30)), n_workers=workers)
     for i, g in enumerate(gs):           # first step of every scene: buffers become resident
@@ -377,7 +415,7 @@ def run_serving(seed, count=256, requests=512, workers=12, budget_gb=150.0, load
     lat = np.array(lat) * 1e3
     return {"value": sum(scs[i].n for i in pick) / wall, "unit": UNIT, "scenes": count,
             "resident_particles": sum(sc.n for sc in scs), "resident_footprint_gb": footprint / 2 ** 30,
-            "requests": requests, "workers": workers, "budget_gb": budget_gb,
+            "requests": requests, "workers": workers, "launch_flags": flags, "budget_gb": budget_gb,
             "capacity_requests_per_s": cap_rate, "capacity_particle_steps_per_s": cap_particles,
             "offered_load": load, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "peak_in_flight_gb": info["peak_in_flight_bytes"] / 2 ** 30,
@@ -446,6 +484,7 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-solvers", action="store_true", help="skip the HOT / PN-PCG / PN-MGPCG comparison")
     ap.add_argument("--serve-scenes", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--profile-run", action="store_true",
@@ -455,7 +494,7 @@ def main():
     if args.small:
         args.workload = "cube8k"
     if args.profile_run:
-        args.no_mixed = args.no_e2e = args.no_cpu = args.no_batch = args.no_serve = True
+        args.no_mixed = args.no_e2e = args.no_cpu = args.no_batch = args.no_serve = args.no_solvers = True
     elif args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -498,12 +537,16 @@ def main():
                                             traffic_key="two_bars_2m_mixed_bytes_per_vcycle"),
                  "kernel_ms": {k: round(v["ms"], 3) for k, v in r2["breakdown"].items()},
                  "clocks": r2["clocks"]}
-    batching = serving = None
+    batching = serving = solvers = None
     if args.workload == "two_bars_600k" and args.precision == 0:
+        if not args.no_solvers:
+            solvers = run_solvers(rank)
         if not args.no_batch:
             batching = run_batching(rank, max(2, args.steps // 2))
         if not args.no_serve:
-            serving = run_serving(rank, count=args.serve_scenes, requests=args.serve_requests)
+            tuned = batching["autotuned"] if batching else {"flags": 0, "workers": 12}
+            serving = run_serving(rank, count=args.serve_scenes, requests=args.serve_requests,
+                                  workers=tuned["workers"], flags=tuned["flags"])
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline_sample()
@@ -518,7 +561,7 @@ def main():
             "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "roofline": roof,
             "lbfgs_loop_on_device": r["device_loop"],
             "kernel_ms_one_step": {k: round(v["ms"], 3) for k, v in r["breakdown"].items()},
-            "clocks": r["clocks"], "mixed": mixed, "batching": batching, "serving": serving,
+            "clocks": r["clocks"], "mixed": mixed, "batching": batching, "serving": serving, "solvers": solvers,
             "cpu_baseline": cpu}
     print(json.dumps(line))
 

@@ -264,6 +264,21 @@ mpm_status mpm_scene_footprint(mpm_scene_t s, int64_t *bytes);
  * failing scene's status (mpm_last_error(NULL) names the scene). */
 mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats);
 
+/* Launch-configuration autotuner for batched stepping (configuration 4 of the
+ * benchmark set: many small scenes whose kernels should overlap).  Runs
+ * `steps` real batched steps under each candidate -- the V-cycle as a CUDA
+ * graph with one cooperative launch per smoothing sweep (options bits 0 and
+ * 2 clear), the V-cycle launched eagerly (bit 0), eagerly with one launch
+ * per Gauss-Seidel color (bits 0 and 2) -- with half and all of the host
+ * cores as worker threads, then keeps the fastest: the scenes' bits 0 and 2
+ * are set to it and mpm_step_batch uses its worker count from then on.  The
+ * candidates differ in launch boundaries only, so the tuning steps are
+ * ordinary steps of the scenes (steps x 3 x the number of distinct worker
+ * counts).  Outputs (may be NULL): the chosen bits, workers, particle-steps/s
+ * and the number of steps each scene took while tuning. */
+mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int32_t *flags_out,
+                              int32_t *workers_out, double *rate_out, int32_t *steps_run_out);
+
 /* Continuous-batching step server (serving many resident scenes).  Requests
  * (one implicit step of a scene each) queue in FIFO order and are admitted
  * when a worker is free, the scene is not already being stepped, and the

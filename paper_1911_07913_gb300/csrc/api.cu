@@ -3,6 +3,7 @@
 // The host issues kernels and takes the solver's scalar decisions (loop
 // termination, line-search acceptance, L-BFGS pair acceptance); every vector
 // and particle operation runs on the device.
+#include <chrono>
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -664,16 +665,27 @@ mpm_status mpm_step(mpm_scene_t sc, mpm_step_stats *st) {
   });
 }
 
+// Worker threads of mpm_step_batch: set by mpm_batch_autotune, else one per
+// host core (a step blocks its thread in stream synchronisations, and more
+// threads than cores only spin against each other).
+static std::atomic<int> g_batch_workers{0};
+
+static int batch_workers(int n) {
+  int w = g_batch_workers.load();
+  if (w <= 0) {
+    const unsigned hc = std::thread::hardware_concurrency();
+    w = hc ? (int)hc : 8;
+  }
+  return std::max(1, std::min(n, w));
+}
+
 mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats) {
   if (n < 0 || (n > 0 && !scenes)) {
     g_last_error = "bad batch";
     return MPM_ERR_INVALID_ARG;
   }
   std::vector<mpm_status> res(n, MPM_OK);
-  // one worker per host core at most: a step blocks its thread in stream
-  // synchronisations, and more threads than cores only spin against each other
-  const unsigned hc = std::thread::hardware_concurrency();
-  const int workers = std::max(1, std::min<int>(n, hc ? (int)hc : 8));
+  const int workers = batch_workers(n);
   std::atomic<int> next{0};
   std::vector<std::thread> th;
   th.reserve(workers);
@@ -691,6 +703,68 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
       g_last_error = "scene " + std::to_string(i) + ": " + reinterpret_cast<Scene *>(scenes[i])->last_error;
       return res[i];
     }
+  return MPM_OK;
+}
+
+// Launch configurations tried by mpm_batch_autotune: V-cycle as a CUDA graph
+// with one cooperative launch per Gauss-Seidel sweep (the single-scene
+// default); V-cycle launched eagerly (no per-step graph capture, which
+// serialises host threads); eager with one launch per color (no cooperative
+// launches, whose co-residency requirement keeps small scenes' kernels from
+// overlapping).  None changes the arithmetic.
+static const int32_t kTuneModes[3] = {0, 1, 5};
+
+mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int32_t *flags_out,
+                              int32_t *workers_out, double *rate_out, int32_t *steps_run_out) {
+  if (n <= 0 || !scenes || steps < 1) {
+    g_last_error = "bad batch";
+    return MPM_ERR_INVALID_ARG;
+  }
+  int64_t particles = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!scenes[i]) {
+      g_last_error = "NULL scene in batch";
+      return MPM_ERR_INVALID_ARG;
+    }
+    particles += reinterpret_cast<Scene *>(scenes[i])->np;
+  }
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int cores = hc ? (int)hc : 8;
+  std::vector<int> wl = {std::max(1, cores / 2), cores};
+  if (wl[0] == wl[1]) wl.pop_back();
+  double best = -1.0;
+  int best_mode = 0, best_w = cores, runs = 0;
+  for (int mode : kTuneModes) {
+    for (int w : wl) {
+      for (int i = 0; i < n; ++i) {
+        Scene *s = reinterpret_cast<Scene *>(scenes[i]);
+        s->opts.flags = (s->opts.flags & ~5) | mode;
+      }
+      g_batch_workers.store(w);
+      const auto t0 = std::chrono::steady_clock::now();
+      for (int k = 0; k < steps; ++k) {
+        const mpm_status r = mpm_step_batch(scenes, n, nullptr);
+        if (r != MPM_OK) return r;
+        ++runs;
+      }
+      const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      const double rate = (double)particles * steps / secs;
+      if (rate > best) {
+        best = rate;
+        best_mode = mode;
+        best_w = w;
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    Scene *s = reinterpret_cast<Scene *>(scenes[i]);
+    s->opts.flags = (s->opts.flags & ~5) | best_mode;
+  }
+  g_batch_workers.store(best_w);
+  if (flags_out) *flags_out = best_mode;
+  if (workers_out) *workers_out = best_w;
+  if (rate_out) *rate_out = best;
+  if (steps_run_out) *steps_run_out = runs;
   return MPM_OK;
 }
 

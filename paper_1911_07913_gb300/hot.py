@@ -27,6 +27,7 @@ EXPORTED = ["mpm_set_allocator", "mpm_create_scene", "mpm_destroy_scene", "mpm_l
             "mpm_set_options", "mpm_p2g", "mpm_build_hierarchy", "mpm_solve_step", "mpm_g2p",
             "mpm_step", "mpm_get_state", "mpm_set_state", "mpm_get_grid", "mpm_eval_energy",
             "mpm_eval_gradient", "mpm_get_hessian", "mpm_apply_vcycle", "mpm_get_trace", "mpm_get_inner_iters",
+            "mpm_batch_autotune",
             "mpm_scene_footprint", "mpm_step_batch", "mpm_profile", "mpm_profile_read",
             "mpm_kernel_launch_count", "mpm_particle_energy_noalloc", "mpm_server_create",
             "mpm_server_submit", "mpm_server_poll", "mpm_server_info", "mpm_server_destroy"]
@@ -124,6 +125,8 @@ def load(install_torch_allocator: bool = True):
     lib.mpm_get_inner_iters.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p]
     lib.mpm_scene_footprint.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
     lib.mpm_step_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(mpm_step_stats)]
+    lib.mpm_batch_autotune.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_int32)]
     lib.mpm_set_allocator.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.mpm_profile.argtypes = [C.c_void_p, C.c_int32, C.c_char_p]
     lib.mpm_profile_read.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p,
@@ -470,6 +473,19 @@ class StepServer:
 
 def kernel_launch_count() -> int:
     return int(load().mpm_kernel_launch_count())
+
+
+def batch_autotune(scene_list, steps: int = 1) -> dict:
+    """Times real batched steps under each launch configuration and keeps the
+    fastest (see mpm_batch_autotune); returns the choice."""
+    lib = load()
+    n = len(scene_list)
+    hs = (C.c_void_p * n)(*[s.h for s in scene_list])
+    fl, wk, rate, ran = C.c_int32(), C.c_int32(), C.c_double(), C.c_int32()
+    code = lib.mpm_batch_autotune(hs, n, steps, C.byref(fl), C.byref(wk), C.byref(rate), C.byref(ran))
+    if code != OK:
+        raise HotError(code, lib.mpm_last_error(None).decode())
+    return {"flags": fl.value, "workers": wk.value, "particle_steps_per_s": rate.value, "steps_run": ran.value}
 
 
 def step_batch(scene_list, check=True):

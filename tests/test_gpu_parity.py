@@ -362,6 +362,26 @@ def test_batch_results_match_individual_steps(hot):
         g.close()
 
 
+def test_batch_autotune_steps_are_ordinary_steps(hot):
+    """The autotuner's timing runs are real steps under launch configurations
+    that share their arithmetic: after it, each scene is where the same
+    number of plain single-scene steps takes it."""
+    opts = scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=4e-3, levels=2)
+    scs = [scenes.cube_scene(seed=20 + k, res=16, cube_lo=(5, 4, 5), side=3 + k % 2) for k in range(3)]
+    tuned = [hot.HotScene(sc, opts) for sc in scs]
+    plain = [hot.HotScene(sc, opts) for sc in scs]
+    choice = hot.batch_autotune(tuned, 1)
+    assert choice["flags"] in (0, 1, 5) and choice["workers"] >= 1 and choice["particle_steps_per_s"] > 0
+    for g in plain:
+        for _ in range(choice["steps_run"]):
+            g.step()
+    for a, b in zip(tuned, plain):
+        sa, sb = a.get_state(), b.get_state()
+        assert rel(sa["x"], sb["x"]) < 1e-12 and rel(sa["v"], sb["v"]) < 1e-9
+        a.close()
+        b.close()
+
+
 def test_server_results_match_alone_and_admission(hot):
     """Serving: step requests for several resident scenes, submitted in an
     interleaved order and run concurrently by the server, give each scene the
