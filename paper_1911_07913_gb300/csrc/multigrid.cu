@@ -1055,10 +1055,6 @@ void finalize_values(Scene &s, Hier<T> &h, int m) {
 namespace {
 const char *const SWEEP_SCOPE[8] = {"sgs_l0", "sgs_l1", "sgs_l2", "sgs_l3", "sgs_l4", "sgs_l5", "sgs_l6", "sgs_l7"};
 
-// Symmetric Gauss-Seidel (Alg. 2): colors 0..26, then 26..0.  The backward
-// sweep leaves out its first non-empty color: it is the forward sweep's last,
-// and rows of one color are not coupled, so a second update in a row
-// recomputes the same values from the same inputs.
 template <class T>
 int persistent_blocks() {
   static std::atomic<int> cached{-1};
