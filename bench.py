@@ -126,6 +126,11 @@ def max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
+def job_throughput(units_per_rank: int, ws: int, steps: int, t_max_ms: float) -> float:
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * ws * steps / (t_max_ms / 1e3)
+
+
 def barrier(ws: int):
     if ws > 1:
         import torch.distributed as dist
@@ -520,7 +525,7 @@ def main():
                 sample_clocks=not args.profile_run, profile_run=args.profile_run)
     barrier(ws)
     t_max = max_over_ranks(r["total_ms"], ws)
-    value = sc.n * ws * args.steps / (t_max / 1e3)
+    value = job_throughput(sc.n, ws, args.steps, t_max)
     roof = roofline_entry(args.dominant, r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
                           traffic_key=f"{args.workload}_{'fp64' if opts.precision == 0 else 'mixed'}_bytes_per_vcycle")
     mixed = None
