@@ -72,6 +72,7 @@ template <class T>
 struct Hier {
   Vals<T> L[MAX_LEVELS];
   DBuf<T> A45;                         // per-particle projected stiffness
+  DBuf<T> rap_t;                       // Galerkin product, first factor: H R^T per fine row (576 values)
   DBuf<T> x, r, z, p, Ap;              // coarsest PCG vectors
   DBuf<double> part;                   // PCG partial sums
   DBuf<unsigned int> bar;              // grid barrier words
@@ -82,20 +83,20 @@ struct Hier {
   size_t cl_smem = 0;                  // 0: level does not fit one cluster
   void set_stream(cudaStream_t st) {
     for (auto &l : L) l.set_stream(st);
-    A45.st = x.st = r.st = z.st = p.st = Ap.st = st;
+    A45.st = x.st = r.st = z.st = p.st = Ap.st = rap_t.st = st;
     part.st = st;
     bar.st = st;
     cg_log.st = st;
   }
   size_t bytes() const {
-    size_t b = A45.bytes() + x.bytes() + r.bytes() + z.bytes() + p.bytes() + Ap.bytes() +
+    size_t b = A45.bytes() + rap_t.bytes() + x.bytes() + r.bytes() + z.bytes() + p.bytes() + Ap.bytes() +
                part.bytes() + bar.bytes() + cg_log.bytes();
     for (auto &l : L) b += l.bytes();
     return b;
   }
   void release() {
     for (auto &l : L) l.release();
-    A45.release(); x.release(); r.release(); z.release(); p.release(); Ap.release();
+    A45.release(); rap_t.release(); x.release(); r.release(); z.release(); p.release(); Ap.release();
     part.release(); bar.release(); cg_log.release();
   }
 };

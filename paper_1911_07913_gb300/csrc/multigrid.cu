@@ -172,60 +172,98 @@ __global__ void k_pattern_rap(int64_t nc, const int *__restrict__ ccoords, const
 
 __device__ __forceinline__ float embed_w(int d) { return d == 0 ? 1.0f : 0.5f; }
 
-// numeric Galerkin product H^{m+1} = R H^m R^T, one CTA per coarse row J,
-// its 125 slots accumulated in shared memory
+// Numeric Galerkin product H^{m+1} = R H^m R^T in two gathers, no atomics
+// (every sum has one owner and a fixed order, so the hierarchy is bitwise
+// reproducible):
+//   T_aK   = sum_c H_ac R_Kc   for each fine row a and the coarse nodes K of
+//            its window: fine couplings reach c in a +- 2 per axis, whose
+//            parents K (|c - 2K| <= 1) lie in [floor(a/2) - 1, floor(a/2) + 2],
+//            a 4^3 window; stored entry-major, T[a][e][window slot];
+//   H_JK   = sum_a R_Ja T_aK   over the 27 fine children a of J.
+// Weights of the linear embedding: 1 on a coarse node, 1/2 between two.
+constexpr int RAP_WIN = 64;
+
+// one warp per fine row a; lane l owns window slots l and l + 32
 template <class T>
-__global__ void __launch_bounds__(128) k_rap(int64_t nc, const int *__restrict__ ccoords, const int *__restrict__ crow_ptr,
-                                             const int *__restrict__ cslotpos, T *__restrict__ cvals,
-                                             const int *__restrict__ fmap, Dims fd, const int *__restrict__ fcoords,
-                                             const int *__restrict__ frow_ptr, const int *__restrict__ fcols,
-                                             const T *__restrict__ fvals) {
-  __shared__ T acc[NSLOT * 9];
-  const int64_t J = blockIdx.x;
-  for (int k = threadIdx.x; k < NSLOT * 9; k += 128) acc[k] = T(0);
-  __syncthreads();
-  int cj[3] = {ccoords[3 * J], ccoords[3 * J + 1], ccoords[3 * J + 2]};
-  for (int o = 0; o < 27; ++o) {
-    int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-    int a[3] = {2 * cj[0] + ox, 2 * cj[1] + oy, 2 * cj[2] + oz};
-    if (a[0] < 0 || a[1] < 0 || a[2] < 0 || a[0] >= fd.d[0] || a[1] >= fd.d[1] || a[2] >= fd.d[2]) continue;
-    int ia = fmap[lin(a[0], a[1], a[2], fd.d)];
-    if (ia < 0) continue;
-    const T rJa = (T)(embed_w(ox) * embed_w(oy) * embed_w(oz));
-    const int rp = frow_ptr[ia], nb = frow_ptr[ia + 1] - rp;
-    const T *fv = fvals + 9 * (int64_t)rp;
-    for (int b = threadIdx.x; b < nb; b += 128) {
-      int c = fcols[rp + b];
-      int cc[3] = {fcoords[3 * c], fcoords[3 * c + 1], fcoords[3 * c + 2]};
-      T h[9];
+__global__ void k_rap_t(int64_t nf, const int *__restrict__ fcoords, const int *__restrict__ frow_ptr,
+                        const int *__restrict__ fslotpos, const T *__restrict__ fvals, T *__restrict__ tout) {
+  const int64_t a = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+  if (a >= nf) return;
+  const int lane = threadIdx.x & 31;
+  const int ca[3] = {fcoords[3 * a], fcoords[3 * a + 1], fcoords[3 * a + 2]};
+  const int rp = frow_ptr[a], nb = frow_ptr[a + 1] - rp;
+  const T *v = fvals + 9 * (int64_t)rp;
+  const int *sp = fslotpos + a * NSLOT;
+  T *to = tout + a * (9 * RAP_WIN);
 #pragma unroll
-      for (int e = 0; e < 9; ++e) h[e] = rJa * fv[e * nb + b];
-      int lo[3], cnt[3];
+  for (int half = 0; half < 2; ++half) {
+    const int q = lane + 32 * half;
+    const int K[3] = {(ca[0] >> 1) - 1 + (q & 3), (ca[1] >> 1) - 1 + ((q >> 2) & 3), (ca[2] >> 1) - 1 + (q >> 4)};
+    int lo[3], hi[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        lo[k] = (cc[k] & 1) ? (cc[k] - 1) >> 1 : cc[k] >> 1;
-        cnt[k] = (cc[k] & 1) ? 2 : 1;
-      }
-      for (int z = 0; z < cnt[2]; ++z)
-        for (int y = 0; y < cnt[1]; ++y)
-          for (int x = 0; x < cnt[0]; ++x) {
-            int K[3] = {lo[0] + x, lo[1] + y, lo[2] + z};
-            T rKc = (T)(embed_w(cc[0] - 2 * K[0]) * embed_w(cc[1] - 2 * K[1]) * embed_w(cc[2] - 2 * K[2]));
-            int s = (K[0] - cj[0] + 2) + 5 * (K[1] - cj[1] + 2) + 25 * (K[2] - cj[2] + 2);
-            T *dst = acc + 9 * s;
-#pragma unroll
-            for (int e = 0; e < 9; ++e) atomicAdd(dst + e, rKc * h[e]);
-          }
+    for (int k = 0; k < 3; ++k) {   // children c = 2K + oc of K within a +- 2
+      lo[k] = max(-1, ca[k] - 2 * K[k] - 2);
+      hi[k] = min(1, ca[k] - 2 * K[k] + 2);
     }
+    T acc[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) acc[e] = T(0);
+    for (int oz = lo[2]; oz <= hi[2]; ++oz)
+      for (int oy = lo[1]; oy <= hi[1]; ++oy)
+        for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+          const int ex = 2 * K[0] + ox - ca[0], ey = 2 * K[1] + oy - ca[1], ez = 2 * K[2] + oz - ca[2];
+          const int pos = sp[(ex + 2) + 5 * (ey + 2) + 25 * (ez + 2)];
+          if (pos < 0) continue;
+          const T w = (T)(embed_w(ox) * embed_w(oy) * embed_w(oz));
+          const int k = pos - rp;
+#pragma unroll
+          for (int e = 0; e < 9; ++e) acc[e] = fma(w, v[e * nb + k], acc[e]);
+        }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) to[e * RAP_WIN + q] = acc[e];
   }
-  __syncthreads();
+  (void)nb;
+}
+
+// one thread per coarse block (J, K = J + d) of coarse row J
+template <class T>
+__global__ void __launch_bounds__(128) k_rap_r(int64_t nc, const int *__restrict__ ccoords,
+                                               const int *__restrict__ crow_ptr, const int *__restrict__ cslotpos,
+                                               T *__restrict__ cvals, const int *__restrict__ fmap, Dims fd,
+                                               const T *__restrict__ tin) {
+  const int64_t J = blockIdx.x;
+  const int s = threadIdx.x;
+  if (J >= nc || s >= NSLOT) return;
+  const int cpos = cslotpos[J * NSLOT + s];
+  if (cpos < 0) return;
+  const int d[3] = {s % 5 - 2, (s / 5) % 5 - 2, s / 25 - 2};
+  const int cj[3] = {ccoords[3 * J], ccoords[3 * J + 1], ccoords[3 * J + 2]};
+  T acc[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) acc[e] = T(0);
+  for (int o = 0; o < 27; ++o) {
+    const int oa[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+    int q = 0;
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int a = 2 * cj[k] + oa[k];
+      const int qk = d[k] - (oa[k] < 0 ? -1 : 0) + 1;   // K - (floor(a/2) - 1)
+      in = in && a >= 0 && a < fd.d[k] && qk >= 0 && qk < 4;
+      q += qk << (2 * k);
+    }
+    if (!in) continue;
+    const int ia = fmap[lin(2 * cj[0] + oa[0], 2 * cj[1] + oa[1], 2 * cj[2] + oa[2], fd.d)];
+    if (ia < 0) continue;
+    const T w = (T)(embed_w(oa[0]) * embed_w(oa[1]) * embed_w(oa[2]));
+    const T *tr = tin + (int64_t)ia * (9 * RAP_WIN) + q;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) acc[e] = fma(w, tr[e * RAP_WIN], acc[e]);
+  }
   const int rp = crow_ptr[J], nb = crow_ptr[J + 1] - rp;
   T *cv = cvals + 9 * (int64_t)rp;
-  for (int k = threadIdx.x; k < NSLOT * 9; k += 128) {
-    int s = k / 9, e = k % 9;
-    int pos = cslotpos[J * NSLOT + s];
-    if (pos >= 0) cv[e * nb + (pos - rp)] = acc[k];
-  }
+#pragma unroll
+  for (int e = 0; e < 9; ++e) cv[e * nb + (cpos - rp)] = acc[e];
 }
 
 // Inverse of each diagonal block (formed in float64) and the scalar diagonal.
@@ -1031,10 +1069,14 @@ void rap(Scene &s, Hier<T> &h, int m) {
   Vals<T> &VC = h.L[m + 1];
   VC.vals.ensure(9 * (size_t)C.nnzb + 9);
   if (C.n == 0) return;
+  h.rap_t.ensure((size_t)9 * RAP_WIN * F.n + 9 * RAP_WIN);
   ProfScope prof_(s, "rap");
-  k_rap<T><<<(unsigned)C.n, 128, 0, s.st>>>(C.n, C.coords.p, C.row_ptr.p, C.slotpos.p, VC.vals.p, F.map.p, dims_of(F),
-                                            F.coords.p, F.row_ptr.p, F.cols.p, h.L[m].vals.p);
-  HOT_LAUNCH("k_rap");
+  k_rap_t<T><<<(unsigned)((F.n + WPB - 1) / WPB), NT, 0, s.st>>>(F.n, F.coords.p, F.row_ptr.p, F.slotpos.p,
+                                                                h.L[m].vals.p, h.rap_t.p);
+  HOT_LAUNCH("k_rap_t");
+  k_rap_r<T><<<(unsigned)C.n, 128, 0, s.st>>>(C.n, C.coords.p, C.row_ptr.p, C.slotpos.p, VC.vals.p, F.map.p,
+                                              dims_of(F), h.rap_t.p);
+  HOT_LAUNCH("k_rap_r");
 }
 
 template <class T>
