@@ -375,14 +375,35 @@ __global__ void __launch_bounds__(HNT) k_hessian_cells(const double *__restrict_
 #pragma unroll
     for (int e = 0; e < 9; ++e) atomicAdd(base + e * nb, acc[e]);
   }
-  if (pi != pl) {
-    int rp = row_ptr[rl], nb = row_ptr[rl + 1] - rp;
-    int pos = slotpos[(int64_t)rl * NSLOT + (NSLOT - 1 - s)] - rp;
-    T *base = vals + 9 * (int64_t)rp + pos;
+  // the transposed block (rl, ri) is filled by k_hessian_mirror
+}
+
+// Lower half from the upper: a cell adds pair (i, l) of its stencil only for
+// stencil index i <= l, i.e. for block offsets o = l - i with
+// o_x + 3 o_y + 9 o_z >= 0 (the same sign in every cell), so the blocks with
+// a negative index offset get the transpose of their mirror.  One warp per
+// row; only reads of finished blocks, no atomics.
+template <class T>
+__global__ void k_hessian_mirror(int64_t nn, const int *__restrict__ row_ptr, const int *__restrict__ cols,
+                                 const int *__restrict__ slotpos, T *vals) {
+  const int64_t i = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+  if (i >= nn) return;
+  const int lane = threadIdx.x & 31;
+  const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
+  for (int s = lane; s < NSLOT; s += 32) {
+    const int o[3] = {s % 5 - 2, (s / 5) % 5 - 2, s / 25 - 2};
+    if (o[0] + 3 * o[1] + 9 * o[2] >= 0) continue;
+    const int pos = slotpos[i * NSLOT + s];
+    if (pos < 0) continue;
+    const int j = cols[pos];
+    const int rpj = row_ptr[j], nbj = row_ptr[j + 1] - rpj;
+    const int posj = slotpos[(int64_t)j * NSLOT + (NSLOT - 1 - s)] - rpj;
+    const T *src = vals + 9 * (int64_t)rpj + posj;
+    T *dst = vals + 9 * (int64_t)rp + (pos - rp);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) atomicAdd(base + (3 * b + a) * nb, acc[3 * a + b]);
+      for (int b = 0; b < 3; ++b) dst[(3 * a + b) * nb] = src[(3 * b + a) * nbj];
   }
 }
 
@@ -505,6 +526,9 @@ void hessian_assemble(Scene &s, Hier<T> &h) {
     HOT_LAUNCH("k_hessian_cells");
   }
   if (t.n > 0) {
+    k_hessian_mirror<T><<<(unsigned)((t.n + NT / 32 - 1) / (NT / 32)), NT, 0, s.st>>>(t.n, t.row_ptr.p, t.cols.p,
+                                                                                     t.slotpos.p, L.vals.p);
+    HOT_LAUNCH("k_hessian_mirror");
     k_hessian_finish<T><<<(unsigned)((t.n + NT / 32 - 1) / (NT / 32)), NT, 0, s.st>>>(t.n, t.row_ptr.p, t.cols.p,
                                                                                      s.fixed.p, s.m.p, L.vals.p);
     HOT_LAUNCH("k_hessian_finish");
