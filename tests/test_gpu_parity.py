@@ -292,6 +292,39 @@ def test_empty_scene(hot):
     assert g.grid()["coords"].shape == (0, 3)
 
 
+@pytest.mark.parametrize("solver", [0, 1, 2])
+def test_scene_at_rest_takes_no_iteration(hot, solver):
+    """Degenerate step: no velocity, no gravity, undeformed (F = I, C = 0),
+    away from every boundary: the gradient at dv = 0 is exactly zero, so
+    every solver stops before its first iteration and the particles keep
+    their state bit for bit."""
+    sc = scenes.cube_scene(seed=1, res=32, cube_lo=(12, 12, 12), side=6, vel_amp=0.0, floor_nodes=-1.0,
+                           gravity=(0.0, 0.0, 0.0))
+    sc.v[:] = 0.0
+    g = hot.HotScene(sc, scenes.SolverOptions(eps=1e-7, cn_mode=0, dt=1e-3, levels=2, solver=solver))
+    st = g.step()
+    assert st["status"] == 0 and st["iters"] == 0
+    out = g.get_state()
+    assert np.array_equal(out["x"], sc.x) and np.all(out["v"] == 0.0)
+    assert np.array_equal(out["F"].reshape(-1, 9), sc.F.reshape(-1, 9))
+    g.close()
+
+
+def test_fully_held_scene(hot):
+    """Every active node inside the held wall band: no free node, so the CN
+    test (||g^|| <= eps sqrt(0)) holds at once and the grid velocity is the
+    prescribed zero."""
+    sc = scenes.cube_scene(seed=2, res=16, cube_lo=(1, 1, 1), side=1, vel_amp=0.3)
+    g = hot.HotScene(sc, scenes.SolverOptions(eps=1e-7, cn_mode=0, dt=1e-3, levels=2))
+    g.p2g()
+    gd = g.grid()
+    assert np.all(gd["fixed"] != 0)
+    st = g.solve()
+    assert st["status"] == 0 and st["iters"] == 0
+    assert np.all(g.grid()["v"] == 0.0)
+    g.close()
+
+
 def test_particle_on_cell_centre_gives_zero_mass_nodes(hot):
     sc = scenes.cube_scene(seed=0, res=16, cube_lo=(6, 6, 6), side=1)
     dx = sc.dx
