@@ -961,17 +961,18 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
 
 template <class T>
 int coop_blocks() {
-  static int cached = -1;
-  if (cached < 0) {
+  static std::atomic<int> cached{-1};
+  int c = cached.load();
+  if (c < 0) {
     int per_sm = 0;
     HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_pcg<T>, NT, 0));
     int dev = 0, nsm = 0;
     HOT_CUDA(cudaGetDevice(&dev));
     HOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    cached = per_sm * nsm;
-    if (cached < 1) cached = 1;
+    c = std::max(1, per_sm * nsm);
+    cached.store(c);
   }
-  return cached;
+  return c;
 }
 }  // namespace
 
