@@ -693,6 +693,18 @@ def hot_solve(prob: Problem, opts, replay: Optional[Trace] = None, levels=None):
         if it >= opts.max_iters:
             tr.status = "not_converged"
             break
+        refresh = getattr(opts, "refresh_every", 0)
+        if refresh > 0 and it > 0 and it % refresh == 0:
+            # Extension, not in Alg. 3 (which builds the hierarchy once per
+            # step): rebuild the projected Hessian and its hierarchy at the
+            # current iterate and restart the history.
+            H = prob.hessian(dv)
+            levels = build_hierarchy(prob.g.coords, H, prob.hessian_pattern(), opts.levels)
+            vc_new = VCycle(levels, prob.g.fixed, opts.eps, opts.max_coarse_cg)
+            vc_new.cg_counts = vc.cg_counts
+            vc_new.forced = vc.forced
+            vc = vc_new
+            hist = []
         q = -g
         alph = []
         for (s, y, rho) in reversed(hist):

@@ -105,6 +105,7 @@ class SolverOptions:
                               # coarsest PCG; 2: one launch per SGS color; 3: the same, finest level;
                               # 4: host-driven L-BFGS loop; 5: device-side graph loop always
     solver: int = 0           # 0: HOT (Alg. 3); 1: PN-PCG; 2: PN-MGPCG (Alg. 1, comparison solvers)
+    refresh_every: int = 0    # HOT extension: rebuild the hierarchy at the iterate every k iterations (0: off)
 
 
 def _jittered_block(rng, cell_lo, cell_hi, dx, origin, ppc_axis=2):

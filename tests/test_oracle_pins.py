@@ -620,3 +620,20 @@ def test_pn_replay_reproduces_solve_and_agrees_with_hot():
     # all three solvers stop at the same tolerance on the same problem
     dvh, trh = O.hot_solve(prob, opts)
     assert np.abs(dv - dvh).max() <= 1e-4 * np.abs(dvh).max()
+
+
+def test_hierarchy_refresh_extension_converges_and_replays():
+    """The refresh extension (not in Alg. 3): rebuilding the hierarchy at the
+    iterate every 2 iterations still minimises E -- it meets the dense
+    Newton solution -- and replays exactly."""
+    sc = scenes.tiny_scene(seed=3, res=16, cells=(1, 1, 1), lo=(6, 6, 6), ppc_axis=2,
+                           model=1, E=1e4, F_jitter=0.1)
+    g = O.p2g(sc)
+    prob = O.Problem(sc, g, 2e-2)
+    opts = scenes.SolverOptions(eps=1e-8, cn_mode=1, levels=2, max_iters=200, refresh_every=2)
+    dv, tr = O.hot_solve(prob, opts)
+    assert tr.status == "ok" and tr.iters > 2
+    ref = dense_newton(prob)
+    np.testing.assert_allclose(dv, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+    dv2, _ = O.hot_solve(prob, opts, replay=tr)
+    np.testing.assert_array_equal(dv2, dv)
