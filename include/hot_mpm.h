@@ -132,6 +132,12 @@ typedef struct {
                             rebuilt every Newton iteration, Sec. 4.3).  For 1 and 2, max_iters
                             caps the Newton iterations and each CG run is capped at
                             MPM_PN_MAX_CG iterations. */
+  int32_t refresh_every; /* HOT only; an extension, 0 = Alg. 3 as printed (the hierarchy is
+                            built once per step): every refresh_every iterations without
+                            convergence, rebuild the projected Hessian and its hierarchy at
+                            the current iterate and restart the L-BFGS history.  Runs the
+                            host-driven loop. */
+  int32_t reserved;
 } mpm_solver_opts;
 
 #define MPM_PN_MAX_CG 10000

@@ -155,6 +155,7 @@ void validate_opts(const mpm_solver_opts *o) {
   if (o->max_iters < 1 || o->max_ls < 1) fail(MPM_ERR_INVALID_ARG, "max_iters and max_ls must be >= 1");
   if (o->max_coarse_cg < 0) fail(MPM_ERR_INVALID_ARG, "max_coarse_cg must be >= 0");
   if (o->solver < 0 || o->solver > 2) fail(MPM_ERR_INVALID_ARG, "solver must be 0 (HOT), 1 (PN-PCG) or 2 (PN-MGPCG)");
+  if (o->refresh_every < 0) fail(MPM_ERR_INVALID_ARG, "refresh_every must be >= 0");
   if (o->dt <= 0.0 && !(o->fps > 0.0 && o->cfl > 0.0)) fail(MPM_ERR_INVALID_ARG, "need dt > 0 or fps, cfl > 0");
 }
 
@@ -332,6 +333,11 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
     if (it >= s.opts.max_iters) {
       status = MPM_ERR_NOT_CONVERGED;
       break;
+    }
+    if (s.opts.refresh_every > 0 && it > 0 && it % s.opts.refresh_every == 0) {
+      // extension: the hierarchy at the current iterate, a fresh history
+      pn_rebuild_values(s);
+      s.hist_n = 0;
     }
     // two-loop recursion around the V-cycle initializer (Alg. 3)
     scale_copy(s, s.q.p, -1.0, s.g.p, n3);

@@ -348,6 +348,7 @@ void pn_prepare(Scene &s);          // captures the CG loop (buffers, V-cycle pl
 int pn_cg_run(Scene &s);            // CG on H p = -g into s.pdir; returns its iterations
 void pn_release(Scene &s);
 void pn_rebuild_values(Scene &s);   // projected Hessian (and hierarchy) at the current s.Lv
+                                    // (also the refresh extension of the L-BFGS loop)
 void note_launches(long long n);   // adds to the kernel launch counter
 long long launch_count();
 

@@ -234,7 +234,7 @@ void pn_release(Scene &s) {
   s.pn_graph.graph = nullptr;
 }
 
-// the projected Hessian (and for PN-MGPCG its Galerkin hierarchy) at the
+// the projected Hessian (and, but for PN-PCG, its Galerkin hierarchy) at the
 // current iterate: the stiffness is taken at F from s.Lv, the velocity
 // gradient of v^n + dv
 void pn_rebuild_values(Scene &s) {
@@ -242,7 +242,7 @@ void pn_rebuild_values(Scene &s) {
     particle_stiffness<double>(s, s.hd);
     hessian_assemble<double>(s, s.hd);
     finalize_values<double>(s, s.hd, 0);
-    if (s.opts.solver == 2)
+    if (s.opts.solver != 1)   // PN-PCG uses the fine matrix only
       for (int m = 0; m + 1 < s.nlev; ++m) {
         rap<double>(s, s.hd, m);
         finalize_values<double>(s, s.hd, m + 1);
@@ -251,7 +251,7 @@ void pn_rebuild_values(Scene &s) {
     particle_stiffness<float>(s, s.hf);
     hessian_assemble<float>(s, s.hf);
     finalize_values<float>(s, s.hf, 0);
-    if (s.opts.solver == 2)
+    if (s.opts.solver != 1)
       for (int m = 0; m + 1 < s.nlev; ++m) {
         rap<float>(s, s.hf, m);
         finalize_values<float>(s, s.hf, m + 1);

@@ -214,6 +214,24 @@ def test_projected_newton_replay_parity(hot, name, solver):
         assert np.sqrt(np.sum(gr * gr)) <= opts.eps * np.sqrt(np.sum(prob.gradient(0 * dv) ** 2)) * (1 + 1e-6)
 
 
+def test_refresh_extension_replay_parity(hot):
+    """Hierarchy refresh every 3 iterations (extension of Alg. 3): the oracle
+    with the same refresh replays the GPU's decisions to the same Δv."""
+    sc, opts = SCENES["bars_nh_cn"]
+    opts = scenes.SolverOptions(**{**opts.__dict__, "refresh_every": 3})
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    st = g.solve()
+    assert st["status"] == 0 and st["iters"] > 3 and st["device_loop"] == 0
+    tr = g.trace()
+    dv = g.grid()["dv"]
+    g.close()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, st["dt"])
+    dvo, _ = O.hot_solve(prob, opts, replay=replay_trace(tr))
+    assert rel(dv, dvo) < 1e-9
+
+
 def replay_trace(tr):
     return O.Trace(iters=tr["iters"], alphas=tr["alphas"], ls_trials=tr["ls_trials"],
                    cg_counts=tr["cg_counts"], skipped=tr["skipped"], fallback=tr["fallback"])
