@@ -642,6 +642,7 @@ class Trace:
     fallback: List[int] = dataclasses.field(default_factory=list)
     norms: List[float] = dataclasses.field(default_factory=list)
     energies: List[float] = dataclasses.field(default_factory=list)
+    inner: List[int] = dataclasses.field(default_factory=list)   # CG counts after a fallback to PN-MGPCG
     status: str = "ok"
 
 
@@ -693,6 +694,25 @@ def hot_solve(prob: Problem, opts, replay: Optional[Trace] = None, levels=None):
         if it >= opts.max_iters:
             tr.status = "not_converged"
             break
+        fb_after = getattr(opts, "fallback_after", 0)
+        if fb_after > 0 and it >= fb_after:
+            # Extension, not in Alg. 3: a step that has not converged after
+            # fallback_after L-BFGS iterations is finished by PN-MGPCG (Alg. 1)
+            # from the current iterate.
+            rp = None
+            if replay is not None:
+                rp = PNTrace(iters=replay.iters, alphas=replay.alphas, ls_trials=replay.ls_trials,
+                             cg_iters=replay.inner)
+            dv, ptr = pn_solve(prob, opts, "mg", replay=rp, dv0=dv, it0=it, g1n=g1n, vc_forced=vc.forced)
+            tr.alphas.extend(ptr.alphas)
+            tr.ls_trials.extend(ptr.ls_trials)
+            tr.inner = list(ptr.cg_iters)
+            tr.energies.extend(ptr.energies[1:])
+            tr.norms.extend(ptr.norms[1:])
+            tr.status = ptr.status
+            tr.iters = ptr.iters
+            tr.cg_counts = list(vc.cg_counts) + list(ptr.vc_cg_counts)
+            return dv, tr
         refresh = getattr(opts, "refresh_every", 0)
         if refresh > 0 and it > 0 and it % refresh == 0:
             # Extension, not in Alg. 3 (which builds the hierarchy once per
@@ -814,7 +834,8 @@ class PNTrace:
 
 
 def pn_solve(prob: Problem, opts, precond: str = "jacobi", max_cg: int = 10000,
-             replay: Optional[PNTrace] = None):
+             replay: Optional[PNTrace] = None, dv0=None, it0: int = 0, g1n: Optional[float] = None,
+             vc_forced: Optional[list] = None):
     """Alg. 1: Newton iterations on E(dv), each solving the projected Hessian
     system H p = -g at the current dv (Teran projection, Dirichlet projection)
     inexactly by PCG (pn_pcg), then the backtracking line search from alpha =
@@ -822,17 +843,23 @@ def pn_solve(prob: Problem, opts, precond: str = "jacobi", max_cg: int = 10000,
     diagonal of H (PN-PCG); "mg": one V-cycle (Alg. 2, same coarsest solve)
     of the Galerkin hierarchy built from that H (PN-MGPCG).  With ``replay``
     the CG iteration counts (and coarsest-PCG counts) and step lengths of
-    another implementation are imposed.  Returns (dv, trace)."""
+    another implementation are imposed.  dv0, it0, g1n: continue another
+    solver's iterations from its iterate (iteration numbers, and the replayed
+    step lengths, continue from it0; replay.cg_iters counts from it0);
+    vc_forced: a coarsest-PCG count list shared with that solver.
+    Returns (dv, trace)."""
     n = prob.n
-    dv = np.zeros((n, 3))
+    dv = np.zeros((n, 3)) if dv0 is None else dv0.copy()
     g = prob.gradient(dv)
-    g1n = float(np.sqrt(np.sum(g * g)))
+    if g1n is None:
+        g1n = float(np.sqrt(np.sum(g * g)))
     E = prob.energy(dv)
     tr = PNTrace()
     tr.energies.append(E)
     pattern = prob.hessian_pattern() if precond == "mg" else None
-    vc_forced = list(replay.vc_cg_counts) if replay is not None else None
-    it = 0
+    if vc_forced is None and replay is not None:
+        vc_forced = list(replay.vc_cg_counts)
+    it = it0
     while True:
         if opts.cn_mode == 0:
             nrm, nfree = prob.cn_norm(g)
@@ -858,7 +885,7 @@ def pn_solve(prob: Problem, opts, precond: str = "jacobi", max_cg: int = 10000,
             if vc_forced is not None:
                 vc.forced = vc_forced           # shared: consumed across Newton iterations
             M = lambda r: vc(r.reshape(-1, 3)).ravel()  # noqa: E731
-        forced = replay.cg_iters[it] if replay is not None else None
+        forced = replay.cg_iters[it - it0] if replay is not None else None
         p, its = pn_pcg(H, -g, M, opts.eps, max_cg, forced)
         tr.cg_iters.append(its)
         if precond == "mg":

@@ -106,6 +106,7 @@ class SolverOptions:
                               # 4: host-driven L-BFGS loop; 5: device-side graph loop always
     solver: int = 0           # 0: HOT (Alg. 3); 1: PN-PCG; 2: PN-MGPCG (Alg. 1, comparison solvers)
     refresh_every: int = 0    # HOT extension: rebuild the hierarchy at the iterate every k iterations (0: off)
+    fallback_after: int = 0   # HOT extension: finish an unconverged step with PN-MGPCG after k iterations
 
 
 def _jittered_block(rng, cell_lo, cell_hi, dx, origin, ppc_axis=2):

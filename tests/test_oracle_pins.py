@@ -637,3 +637,22 @@ def test_hierarchy_refresh_extension_converges_and_replays():
     np.testing.assert_allclose(dv, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
     dv2, _ = O.hot_solve(prob, opts, replay=tr)
     np.testing.assert_array_equal(dv2, dv)
+
+
+def test_fallback_extension_finishes_with_newton_and_replays():
+    """The fallback extension (not in Alg. 3): after 2 L-BFGS iterations the
+    step continues as PN-MGPCG from the iterate; it still reaches the dense
+    Newton solution and replays exactly."""
+    sc = scenes.tiny_scene(seed=3, res=16, cells=(1, 1, 1), lo=(6, 6, 6), ppc_axis=2,
+                           model=1, E=1e4, F_jitter=0.1)
+    g = O.p2g(sc)
+    prob = O.Problem(sc, g, 2e-2)
+    opts = scenes.SolverOptions(eps=1e-8, cn_mode=1, levels=2, max_iters=200, fallback_after=2)
+    dv, tr = O.hot_solve(prob, opts)
+    assert tr.status == "ok" and tr.iters > 2 and len(tr.inner) == tr.iters - 2
+    assert len(tr.skipped) == 2 and len(tr.alphas) == tr.iters
+    ref = dense_newton(prob)
+    np.testing.assert_allclose(dv, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+    assert np.all(np.diff(tr.energies) <= 0)
+    dv2, _ = O.hot_solve(prob, opts, replay=tr)
+    np.testing.assert_array_equal(dv2, dv)
