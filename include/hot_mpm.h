@@ -137,7 +137,10 @@ typedef struct {
                             convergence, rebuild the projected Hessian and its hierarchy at
                             the current iterate and restart the L-BFGS history.  Runs the
                             host-driven loop. */
-  int32_t reserved;
+  int32_t fallback_after; /* HOT only; an extension, 0 = off: a step that has not converged
+                             after fallback_after L-BFGS iterations continues as PN-MGPCG
+                             (Alg. 1) from the current iterate, within the same max_iters.
+                             Runs the host-driven loop. */
 } mpm_solver_opts;
 
 #define MPM_PN_MAX_CG 10000

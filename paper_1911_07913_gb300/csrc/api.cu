@@ -156,6 +156,7 @@ void validate_opts(const mpm_solver_opts *o) {
   if (o->max_coarse_cg < 0) fail(MPM_ERR_INVALID_ARG, "max_coarse_cg must be >= 0");
   if (o->solver < 0 || o->solver > 2) fail(MPM_ERR_INVALID_ARG, "solver must be 0 (HOT), 1 (PN-PCG) or 2 (PN-MGPCG)");
   if (o->refresh_every < 0) fail(MPM_ERR_INVALID_ARG, "refresh_every must be >= 0");
+  if (o->fallback_after < 0) fail(MPM_ERR_INVALID_ARG, "fallback_after must be >= 0");
   if (o->dt <= 0.0 && !(o->fps > 0.0 && o->cfl > 0.0)) fail(MPM_ERR_INVALID_ARG, "need dt > 0 or fps, cfl > 0");
 }
 
@@ -316,6 +317,7 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
     pn_loop(s, E, norms, thr, nrm, it, trials_total, inner_total, status);
   }
   const bool on_device = s.opts.solver == 0 && solve_loop_graph(s, E, norms, thr, E, nrm, it, trials_total, status);
+  bool to_newton = false;   // fallback_after reached (extension)
   while (s.opts.solver == 0 && !on_device) {
     if (!std::isfinite(norms[0]) || !std::isfinite(norms[1]) || !std::isfinite(E)) {
       status = MPM_ERR_NUMERIC;
@@ -332,6 +334,10 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
     if (done) break;
     if (it >= s.opts.max_iters) {
       status = MPM_ERR_NOT_CONVERGED;
+      break;
+    }
+    if (s.opts.fallback_after > 0 && it >= s.opts.fallback_after) {
+      to_newton = true;
       break;
     }
     if (s.opts.refresh_every > 0 && it > 0 && it % s.opts.refresh_every == 0) {
@@ -401,6 +407,18 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
     std::swap(s.g, s.g_new);
     E = E1;
     ++it;
+  }
+  if (to_newton) {
+    // extension: finish the step with PN-MGPCG from the current iterate
+    const int solver = s.opts.solver;
+    s.opts.solver = 2;
+    try {
+      pn_loop(s, E, norms, thr, nrm, it, trials_total, inner_total, status);
+    } catch (...) {
+      s.opts.solver = solver;
+      throw;
+    }
+    s.opts.solver = solver;
   }
   int e = read_errflag(s);
   if (e & DEV_ERR_TIMEOUT) status = MPM_ERR_TIMEOUT;

@@ -141,7 +141,7 @@ struct Counts {
 bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double &E, double &nrm, int &it,
                       int &trials_total, mpm_status &status) {
   if (!s.loop_graph_ok || !s.graphs_ok || s.prof || (s.opts.flags & 17) || s.nn() == 0 ||
-      s.opts.refresh_every > 0)
+      s.opts.refresh_every > 0 || s.opts.fallback_after > 0)
     return false;
   // building the graph costs about as much host time as a handful of host-
   // driven iterations: by default it is used once the scene's previous solve

@@ -62,7 +62,7 @@ class mpm_solver_opts(C.Structure):
                 ("levels", C.c_int32), ("precision", C.c_int32), ("max_iters", C.c_int32),
                 ("max_ls", C.c_int32), ("max_coarse_cg", C.c_int32), ("record_trace", C.c_int32),
                 ("dt", C.c_double), ("fps", C.c_double), ("cfl", C.c_double), ("flags", C.c_int32),
-                ("solver", C.c_int32), ("refresh_every", C.c_int32), ("reserved", C.c_int32)]
+                ("solver", C.c_int32), ("refresh_every", C.c_int32), ("fallback_after", C.c_int32)]
 
 
 class mpm_step_stats(C.Structure):
@@ -187,7 +187,8 @@ def opts_struct(o: _scenes.SolverOptions) -> mpm_solver_opts:
                            precision=o.precision, max_iters=o.max_iters, max_ls=o.max_ls,
                            max_coarse_cg=o.max_coarse_cg, record_trace=1, dt=o.dt, fps=o.fps,
                            cfl=o.cfl, flags=getattr(o, "flags", 0), solver=getattr(o, "solver", 0),
-                           refresh_every=getattr(o, "refresh_every", 0))
+                           refresh_every=getattr(o, "refresh_every", 0),
+                           fallback_after=getattr(o, "fallback_after", 0))
 
 
 def stats_dict(s: mpm_step_stats) -> dict:

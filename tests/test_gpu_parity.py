@@ -232,6 +232,30 @@ def test_refresh_extension_replay_parity(hot):
     assert rel(dv, dvo) < 1e-9
 
 
+def test_fallback_extension_replay_parity(hot):
+    """After 2 L-BFGS iterations the step finishes as PN-MGPCG (extension of
+    Alg. 3): the oracle with the same fallback replays the GPU's decisions
+    (L-BFGS part, then CG counts and step lengths) to the same Δv."""
+    sc, opts = SCENES["bars_nh_cn"]
+    opts = scenes.SolverOptions(**{**opts.__dict__, "fallback_after": 2})
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    st = g.solve()
+    assert st["status"] == 0 and st["iters"] > 2 and st["device_loop"] == 0
+    tr, inner = g.trace(), g.inner_iters()
+    assert len(inner) == st["iters"] - 2
+    dv = g.grid()["dv"]
+    g.close()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, st["dt"])
+    rep = replay_trace(tr)
+    rep.inner = inner
+    dvo, tro = O.hot_solve(prob, opts, replay=rep)
+    assert tro.iters == st["iters"]
+    # the Newton part runs CG: rounding of its inner products, as in the PN replay test
+    assert rel(dv, dvo) < 1e-7
+
+
 def replay_trace(tr):
     return O.Trace(iters=tr["iters"], alphas=tr["alphas"], ls_trials=tr["ls_trials"],
                    cg_counts=tr["cg_counts"], skipped=tr["skipped"], fallback=tr["fallback"])
