@@ -8,7 +8,8 @@
  * update, advection):
  *
  *     mpm_p2g(s);            bin/sort particles, APIC P2G, boundary conditions
- *     mpm_solve_step(s, &st) minimise Eq. 1 with HOT (Alg. 3, V-cycle Alg. 2)
+ *     mpm_solve_step(s, &st) minimise Eq. 1 with HOT (Alg. 3, V-cycle Alg. 2), or
+ *                            with the paper's comparison solvers (Alg. 1) by option
  *     mpm_g2p(s);            APIC G2P, F update, advection
  *
  * or mpm_step() for the three.  All arithmetic runs in the library's CUDA
