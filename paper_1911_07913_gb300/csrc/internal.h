@@ -78,7 +78,8 @@ struct Hier {
   DBuf<unsigned int> bar;              // grid barrier words
   DBuf<int> cg_log;                    // PCG iteration counts; last entry = count
   int cl_level = -1;                   // coarsest level planned for the cluster solver (-1: none)
-  int cl_bounds[9] = {0};
+  int cl_size = 0;                     // CTAs in the cluster (16 or 8)
+  int cl_bounds[17] = {0};
   int cl_rows_max = 0, cl_nb_max = 0;
   size_t cl_smem = 0;                  // 0: level does not fit one cluster
   void set_stream(cudaStream_t st) {

@@ -842,19 +842,57 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
 }
 
 // ---------------------------------------------------------------------------
-// Coarsest level on one thread-block cluster: the level's rows are split
-// over CL CTAs by block count and kept in their shared memory; every CTA holds
-// the whole search direction p.  Partial dot products and each CTA's slice
-// of p are written into the other CTAs' shared memory (distributed shared
-// memory) and cluster.sync() -- a hardware barrier -- separates the phases.
-// Same Jacobi-PCG iteration and stopping rule as k_coarse_pcg.
+// Coarsest level on one thread-block cluster of `cl` CTAs (16 where the part
+// allows a non-portable cluster of that size, else 8): the level's rows are
+// split over the CTAs by block count and kept in their shared memory.  Same
+// Jacobi-PCG iteration and stopping rule as k_coarse_pcg, two hardware cluster
+// barriers per iteration:
+//   1. each CTA forms Ap and the partial p^T Ap of its rows and writes the
+//      partial into every CTA's shared memory (distributed shared memory);
+//   2. after the barrier, each CTA updates x, r, z of its rows, writes its
+//      slice of z and its partial r^T z into every CTA; after the second
+//      barrier every CTA forms the whole of p = z + beta p locally.
+// The scalar arithmetic (sums of the cluster's partials in rank order, alpha,
+// beta, the stopping test) runs in one thread and is read from shared
+// memory: FP64 instructions are scarce on this part (2 FMA per clock per SM),
+// and repeating them in every thread cost more than the iteration's work.
+// Reductions skip the warps whose lanes hold no term.
 // ---------------------------------------------------------------------------
-constexpr int CL = 8;
+constexpr int CLMAX = 16;
 constexpr int CNT = 512;
+constexpr int CNW = CNT / 32;
 constexpr size_t CL_SMEM_MAX = 200 * 1024;
 struct ClusterPlan {
-  int bounds[CL + 1];
+  int bounds[CLMAX + 1];
 };
+
+// Sum over the CTA of per-warp values held in lane 0 of each warp; the total
+// is returned to every lane of warp 0 (fixed order, so bitwise reproducible).
+__device__ __forceinline__ double cta_sum_lane0(double v, double *ws) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < CNW ? ws[lane] : 0.0;
+#pragma unroll
+    for (int o = CNW / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    t = __shfl_sync(0xffffffffu, t, 0);
+  }
+  return t;
+}
+
+// Sum over the CTA of per-thread values that are zero in threads >= nz.
+__device__ __forceinline__ double cta_sum_first(double v, int nz, double *ws) {
+  const int warp = threadIdx.x >> 5;
+  if (warp * 32 < nz) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  } else {
+    v = 0.0;
+  }
+  return cta_sum_lane0(v, ws);
+}
 
 template <class T>
 __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__restrict__ row_ptr,
@@ -866,26 +904,33 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
                                                             int *log_idx, int log_cap) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  __shared__ double sh[CNT];
+  __shared__ double ws[CNW];
+  __shared__ double s_alpha, s_beta;
+  __shared__ int s_stop;
   extern __shared__ __align__(16) unsigned char sm[];
+  const int cl = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
-  double *redA = reinterpret_cast<double *>(sm);
-  double *redB = redA + CL;
-  T *pfull = reinterpret_cast<T *>(redB + CL);
-  T *x = pfull + 3 * R;
+  double *redP = reinterpret_cast<double *>(sm);   // partials p^T Ap, by rank
+  double *redR = redP + CLMAX;                     // partials r^T z, by rank
+  T *pfull = reinterpret_cast<T *>(redR + CLMAX);
+  T *zfull = pfull + 3 * R;
+  T *x = zfull + 3 * R;
   T *r = x + 3 * rows_max;
-  T *z = r + 3 * rows_max;
-  T *Ap = z + 3 * rows_max;
+  T *Ap = r + 3 * rows_max;
   T *dg = Ap + 3 * rows_max;
   T *vals = dg + 3 * rows_max;
   int *rptr = reinterpret_cast<int *>(vals + 9 * (int64_t)nb_max);
   int *cols = rptr + rows_max + 1;
   const int r0 = plan.bounds[rank], r1 = plan.bounds[rank + 1], nr = r1 - r0;
   const int g0 = row_ptr[r0], nbl = row_ptr[r1] - g0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   cluster.sync();   // every CTA of the cluster is running before any remote access
   for (int k = threadIdx.x; k <= nr; k += CNT) rptr[k] = row_ptr[r0 + k] - g0;
+#pragma unroll 4
   for (int k = threadIdx.x; k < nbl; k += CNT) cols[k] = gcols[g0 + k];
+#pragma unroll 8
   for (int k = threadIdx.x; k < 9 * nbl; k += CNT) vals[k] = gvals[9 * (int64_t)g0 + k];
+  // x = 0, r = b, z = D^-1 r (slices to every CTA), partial r^T z
   double acc = 0.0;
   for (int k = threadIdx.x; k < 3 * nr; k += CNT) {
     const T d = gdiag[3 * r0 + k], bk = b[3 * r0 + k];
@@ -893,62 +938,75 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
     x[k] = T(0);
     r[k] = bk;
     const T zk = bk / d;
-    z[k] = zk;
-    for (int dst = 0; dst < CL; ++dst) cluster.map_shared_rank(pfull, dst)[3 * r0 + k] = zk;
+    for (int dst = 0; dst < cl; ++dst) cluster.map_shared_rank(zfull, dst)[3 * r0 + k] = zk;
     acc += (double)bk * (double)zk;
   }
-  double t = block_sum<CNT>(acc, sh);
-  if (threadIdx.x < CL) cluster.map_shared_rank(redA, threadIdx.x)[rank] = t;
+  double t = cta_sum_first(acc, 3 * nr, ws);
+  if (warp == 0 && lane < cl) cluster.map_shared_rank(redR, lane)[rank] = t;
   cluster.sync();
-  double rz = 0.0;
-  for (int k = 0; k < CL; ++k) rz += redA[k];
-  const double bn = sqrt(fmax(rz, 0.0));
-  const double kk = fmax(fmin(0.5, sqrt(fmax(bn, tau))), sizeof(T) == 4 ? 1e-3 : 0.0);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // rz, |b|_D, the tolerance k and the stopping test: one thread
+  double rz = 0.0, bn = 0.0, kk = 0.0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < cl; ++k) rz += redR[k];
+    bn = sqrt(fmax(rz, 0.0));
+    // in float32 a relative residual below ~1e-3 is not reliably reachable
+    kk = fmax(fmin(0.5, sqrt(fmax(bn, tau))), sizeof(T) == 4 ? 1e-3 : 0.0);
+    s_stop = (sqrt(fmax(rz, 0.0)) <= kk * bn || max_iter <= 0) ? 1 : 0;
+  }
+  for (int k = threadIdx.x; k < 3 * R; k += CNT) pfull[k] = zfull[k];   // p = z
+  __syncthreads();
   int it = 0;
-  while (true) {
-    if (sqrt(fmax(rz, 0.0)) <= kk * bn || it >= max_iter) break;
-    acc = 0.0;
-    for (int i = warp; i < nr; i += CNT / 32) {
+  while (!s_stop) {
+    // Ap = H p on this CTA's rows, partial p^T Ap (lanes 0, 8, 16 hold the
+    // three components of a row after the split warp sum)
+    double accw = 0.0;
+    for (int i = warp; i < nr; i += CNW) {
       T a3[3];
-      row_product<T>(i, true, lane, rptr, cols, vals, pfull, false, a3);
-      if (lane == 0) {
-        Ap[3 * i] = a3[0];
-        Ap[3 * i + 1] = a3[1];
-        Ap[3 * i + 2] = a3[2];
-        const T *pp = pfull + 3 * (r0 + i);
-        acc += (double)pp[0] * (double)a3[0] + (double)pp[1] * (double)a3[1] + (double)pp[2] * (double)a3[2];
+      row_partial<T>(i, true, lane, rptr, cols, vals, pfull, false, a3);
+      const T sc = warp_sum3_split<T>(a3, lane);
+      if ((lane & 7) == 0 && lane < 24) {
+        const int c = lane >> 3;
+        Ap[3 * i + c] = sc;
+        accw += (double)pfull[3 * (r0 + i) + c] * (double)sc;
       }
     }
-    t = block_sum<CNT>(acc, sh);
-    if (threadIdx.x < CL) cluster.map_shared_rank(redB, threadIdx.x)[rank] = t;
+    if (warp < nr) accw += __shfl_down_sync(0xffffffffu, accw, 8) + __shfl_down_sync(0xffffffffu, accw, 16);
+    t = cta_sum_lane0(accw, ws);
+    if (warp == 0 && lane < cl) cluster.map_shared_rank(redP, lane)[rank] = t;
     cluster.sync();
-    double pAp = 0.0;
-    for (int k = 0; k < CL; ++k) pAp += redB[k];
-    if (!(pAp > 0.0)) break;
-    const double alpha = rz / pAp;
+    if (threadIdx.x == 0) {
+      double pAp = 0.0;
+      for (int k = 0; k < cl; ++k) pAp += redP[k];
+      s_stop = (pAp > 0.0) ? 0 : 1;
+      s_alpha = rz / pAp;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const T alpha = (T)s_alpha;
     acc = 0.0;
     for (int k = threadIdx.x; k < 3 * nr; k += CNT) {
-      x[k] += (T)alpha * pfull[3 * r0 + k];
-      const T rk = r[k] - (T)alpha * Ap[k];
+      x[k] += alpha * pfull[3 * r0 + k];
+      const T rk = r[k] - alpha * Ap[k];
       r[k] = rk;
       const T zk = rk / dg[k];
-      z[k] = zk;
+      for (int dst = 0; dst < cl; ++dst) cluster.map_shared_rank(zfull, dst)[3 * r0 + k] = zk;
       acc += (double)rk * (double)zk;
     }
-    t = block_sum<CNT>(acc, sh);
-    if (threadIdx.x < CL) cluster.map_shared_rank(redA, threadIdx.x)[rank] = t;
-    cluster.sync();
-    double rz_new = 0.0;
-    for (int k = 0; k < CL; ++k) rz_new += redA[k];
-    const double beta = rz_new / rz;
-    rz = rz_new;
-    for (int k = threadIdx.x; k < 3 * nr; k += CNT) {
-      const T pk = z[k] + (T)beta * pfull[3 * r0 + k];
-      for (int dst = 0; dst < CL; ++dst) cluster.map_shared_rank(pfull, dst)[3 * r0 + k] = pk;
-    }
+    t = cta_sum_first(acc, 3 * nr, ws);
+    if (warp == 0 && lane < cl) cluster.map_shared_rank(redR, lane)[rank] = t;
     cluster.sync();
     ++it;
+    if (threadIdx.x == 0) {
+      double rz_new = 0.0;
+      for (int k = 0; k < cl; ++k) rz_new += redR[k];
+      s_beta = rz_new / rz;
+      rz = rz_new;
+      s_stop = (sqrt(fmax(rz, 0.0)) <= kk * bn || it >= max_iter) ? 1 : 0;
+    }
+    __syncthreads();
+    const T beta = (T)s_beta;
+    for (int k = threadIdx.x; k < 3 * R; k += CNT) pfull[k] = zfull[k] + beta * pfull[k];
+    __syncthreads();
   }
   for (int k = threadIdx.x; k < 3 * nr; k += CNT) xout[3 * r0 + k] = x[k];
   if (rank == 0 && threadIdx.x == 0) {
@@ -1185,59 +1243,72 @@ void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
 }
 
 // Partition of the coarsest level over one cluster, computed once per
-// hierarchy; cl_smem = 0 when the level does not fit (cooperative fallback).
+// hierarchy: 16 CTAs where a non-portable cluster of that size can be
+// resident, else 8; cl_smem = 0 when the level does not fit either
+// (cooperative fallback).
 template <class T>
 void plan_cluster(Scene &s, Hier<T> &h, int m) {
   Topo &t = s.topo[m];
   h.cl_level = m;
   h.cl_smem = 0;
+  h.cl_size = 0;
   const int R = (int)t.n;
   if (R == 0) return;
   std::vector<int> rp(R + 1);
   HOT_CUDA(cudaMemcpyAsync(rp.data(), t.row_ptr.p, sizeof(int) * (R + 1), cudaMemcpyDeviceToHost, s.st));
   HOT_CUDA(cudaStreamSynchronize(s.st));
-  const int64_t B = rp[R];
-  int r = 0;
-  h.cl_bounds[0] = 0;
-  for (int c = 1; c < CL; ++c) {
-    const int64_t target = B * c / CL;
-    while (r < R && rp[r] < target) ++r;
-    h.cl_bounds[c] = r;
-  }
-  h.cl_bounds[CL] = R;
-  int rows_max = 0, nb_max = 0;
-  for (int c = 0; c < CL; ++c) {
-    rows_max = std::max(rows_max, h.cl_bounds[c + 1] - h.cl_bounds[c]);
-    nb_max = std::max(nb_max, rp[h.cl_bounds[c + 1]] - rp[h.cl_bounds[c]]);
-  }
-  size_t bytes = 2 * CL * sizeof(double) + sizeof(T) * (3 * (size_t)R + 5 * 3 * (size_t)rows_max + 9 * (size_t)nb_max) +
-                 sizeof(int) * ((size_t)rows_max + 1 + nb_max) + 64;
-  if (bytes > CL_SMEM_MAX) return;
   // set once, to the maximum: scenes planned on other threads launch the same kernel
   static std::once_flag once;
   std::call_once(once, [] {
     HOT_CUDA(cudaFuncSetAttribute(k_coarse_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)CL_SMEM_MAX));
+    if (cudaFuncSetAttribute(k_coarse_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess)
+      cudaGetLastError();
   });
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CL);
-  cfg.blockDim = dim3(CNT);
-  cfg.dynamicSmemBytes = bytes;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_pcg_cluster<T>, &cfg) != cudaSuccess || nclusters < 1) {
-    cudaGetLastError();
+  const int64_t B = rp[R];
+  for (int cl : {CLMAX, 8}) {
+    int bounds[CLMAX + 1];
+    int r = 0;
+    bounds[0] = 0;
+    for (int c = 1; c < cl; ++c) {
+      const int64_t target = B * c / cl;
+      while (r < R && rp[r] < target) ++r;
+      bounds[c] = r;
+    }
+    bounds[cl] = R;
+    int rows_max = 0, nb_max = 0;
+    for (int c = 0; c < cl; ++c) {
+      rows_max = std::max(rows_max, bounds[c + 1] - bounds[c]);
+      nb_max = std::max(nb_max, rp[bounds[c + 1]] - rp[bounds[c]]);
+    }
+    const size_t bytes = 2 * CLMAX * sizeof(double) +
+                         sizeof(T) * (6 * (size_t)R + 4 * 3 * (size_t)rows_max + 9 * (size_t)nb_max) +
+                         sizeof(int) * ((size_t)rows_max + 1 + nb_max) + 64;
+    if (bytes > CL_SMEM_MAX) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(CNT);
+    cfg.dynamicSmemBytes = bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_pcg_cluster<T>, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    for (int c = 0; c <= cl; ++c) h.cl_bounds[c] = bounds[c];
+    h.cl_size = cl;
+    h.cl_rows_max = rows_max;
+    h.cl_nb_max = nb_max;
+    h.cl_smem = bytes;
     return;
   }
-  h.cl_rows_max = rows_max;
-  h.cl_nb_max = nb_max;
-  h.cl_smem = bytes;
 }
 
 template <class T>
@@ -1252,15 +1323,15 @@ void coarse_solve(Scene &s, Hier<T> &h, int m) {
                                                 : (int)(sizeof(T) == 4 ? std::min<int64_t>(3 * nn, 100) : 3 * nn);
   if (h.cl_smem > 0 && !(s.opts.flags & 2)) {
     ClusterPlan plan;
-    for (int c = 0; c <= CL; ++c) plan.bounds[c] = h.cl_bounds[c];
+    for (int c = 0; c <= h.cl_size; ++c) plan.bounds[c] = h.cl_bounds[c];
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CL);
+    cfg.gridDim = dim3(h.cl_size);
     cfg.blockDim = dim3(CNT);
     cfg.dynamicSmemBytes = h.cl_smem;
     cfg.stream = s.st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.x = h.cl_size;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
