@@ -633,6 +633,7 @@ mpm_status mpm_set_options(mpm_scene_t sc, const mpm_solver_opts *o) {
     if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
     validate_opts(o);
     bool rebuild = o->precision != s->opts.precision || o->levels != s->opts.levels;
+    if (o->flags != s->opts.flags) s->drop_graph();   // launch modes are baked into the V-cycle graph
     s->opts = *o;
     if (rebuild && s->phase >= PH_HIER) s->phase = PH_P2G;
     return MPM_OK;

@@ -705,8 +705,13 @@ __device__ __forceinline__ unsigned bar_load_acquire(const unsigned *bar) {
   return v;
 }
 
-// MULTI: some color has more rows than the grid has warps (further rounds)
-template <class T, bool MULTI>
+// MULTI: some color has more rows than the grid has warps (further rounds).
+// CLUSTER: the grid is one thread-block cluster and the barrier between colors
+// is the hardware cluster barrier, split the same way (arrive with release
+// semantics, load the next row, wait with acquire semantics); for levels whose
+// colors have few rows, where the grid-wide barrier's latency, not the rows'
+// work, sets the time of a color.
+template <class T, bool MULTI, bool CLUSTER = false>
 __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, const int4 *__restrict__ rec,
                                                              const int *__restrict__ cols, const T *__restrict__ vals,
                                                              const T *__restrict__ dinv, const T *__restrict__ b, T *u,
@@ -738,6 +743,15 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, con
       }
     }
     if (k + 1 == plan.steps) break;
+    if (CLUSTER) {
+      // every thread releases its own stores of u; all wait for all
+      __syncwarp();
+      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+      const int4 rn = s_rec[k + 1][warp];
+      if (rn.x >= 0) load_row<T>(R, rn.x, rn.y, rn.z, lane, cols, vals, dinv, b);
+      asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+      continue;
+    }
     __syncthreads();   // the block's updates of this color precede its arrival
     if (threadIdx.x == 0) bar_arrive_release(bar);
     target += (unsigned)G;
@@ -1174,8 +1188,68 @@ int persistent_blocks() {
   return c;
 }
 
+// CTAs of the cluster that runs the sweeps of small levels: 16 where a
+// non-portable cluster of that size can be resident, else 8 (0: none).
+// Measured on the two-bar scenes: with u in global memory, a color behind the
+// cluster barrier costs ~10-16% less than behind the grid barrier when it has
+// a few dozen rows, and more once a color's FP64 rows outgrow 16 SMs (about a
+// hundred rows), hence the row limit.
+constexpr int CLUSTER_SWEEP_ROWS = 64;
+template <class T>
+int sweep_cluster_size() {
+  static std::atomic<int> cached{-1};
+  int c = cached.load();
+  if (c < 0) {
+    c = 0;
+    if (cudaFuncSetAttribute(k_sgs_persistent<T, false, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess)
+      cudaGetLastError();
+    for (int cl : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cl);
+      cfg.blockDim = dim3(SW_NT);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cl;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_sgs_persistent<T, false, true>, &cfg) == cudaSuccess && n >= 1) {
+        c = cl;
+        break;
+      }
+      cudaGetLastError();
+    }
+    cached.store(c);
+  }
+  return c;
+}
+
 template <class T>
 void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const SweepPlan &plan, int max_rows) {
+  // levels whose colors have at most CLUSTER_SWEEP_ROWS rows: one cluster,
+  // hardware cluster barriers between colors (flag bit 6 turns this off)
+  const int CLR = sweep_cluster_size<T>();
+  if (CLR > 0 && !(s.opts.flags & 64) && max_rows <= std::min(CLUSTER_SWEEP_ROWS, CLR * SW_WARPS)) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CLR);
+    cfg.blockDim = dim3(SW_NT);
+    cfg.stream = s.st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CLR;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T, false, true>, plan, (const int4 *)t.color_rec.p,
+                                (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
+                                V.u.p, (unsigned *)nullptr, s.errflag.p));
+    note_launch("k_sgs_persistent");
+    return;
+  }
   // one block per SM at most, and no more blocks than the largest color has rows
   const int G = std::max(1, std::min(persistent_blocks<T>(), max_rows));
   unsigned *bar = h.bar.p + 2;
@@ -1204,7 +1278,8 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
 // sweep leaves out its first non-empty color: it is the forward sweep's last,
 // and rows of one color are not coupled, so a second update in a row
 // recomputes the same values from the same inputs.  Each sweep is one
-// cooperative launch; flag bit 2 makes it one launch per color on every
+// cooperative launch (one cluster launch on levels whose colors fit a
+// cluster's warps); flag bit 2 makes it one launch per color on every
 // level, bit 3 on the finest level only.
 template <class T>
 void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
@@ -1416,6 +1491,7 @@ void vcycle_prepare(Scene &s, Hier<T> &h) {
   h.cg_log.ensure(4097, 1.0);
   h.part.ensure(2 * (size_t)coop_blocks<T>() + 2);
   persistent_blocks<T>();   // occupancy queries before any capture
+  sweep_cluster_size<T>();
   if (h.cl_level != s.nlev - 1) plan_cluster<T>(s, h, s.nlev - 1);
 }
 

@@ -134,11 +134,12 @@ def test_vcycle_matches_oracle_with_same_coarse_count(hot, name):
     assert abs(vc2.cg_counts[0] - its) <= 1
 
 
-@pytest.mark.parametrize("flags", [4, 0, 8])
+@pytest.mark.parametrize("flags", [4, 0, 8, 64])
 def test_vcycle_smoothing_launch_modes(hot, flags):
-    """One launch per color (bit 2), one cooperative launch per sweep
-    (default) and per-color launches on the finest level only (bit 3) apply
-    the same V-cycle."""
+    """One launch per color (bit 2), one launch per sweep (default: a cluster
+    launch on levels whose colors fit a cluster's warps, else cooperative),
+    per-color launches on the finest level only (bit 3) and cooperative
+    launches on every level (bit 6) apply the same V-cycle."""
     sc, opts = SCENES["bars_nh_cn"]
     opts = scenes.SolverOptions(**{**opts.__dict__, "flags": flags})
     g = hot.HotScene(sc, opts)
@@ -154,6 +155,29 @@ def test_vcycle_smoothing_launch_modes(hot, flags):
     vc.forced = [its]
     assert rel(u, vc(b)) < 1e-9
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vcycle_launch_modes_bitwise(hot, precision):
+    """Every sweep launch mode runs the same per-row arithmetic in the same
+    color order: on one hierarchy, the V-cycle's output is bitwise the same
+    with the default launches (cluster sweeps on levels with few rows per
+    color), cooperative sweeps on every level (bit 6) and one launch per
+    color (bit 2)."""
+    sc, opts = SCENES["bars_nh_cn"]
+    base = {**opts.__dict__, "precision": precision}
+    g = hot.HotScene(sc, scenes.SolverOptions(**base))
+    g.p2g()
+    g.build_hierarchy()
+    b = np.random.default_rng(5).normal(size=(len(g.grid()["m"]), 3))
+    out = []
+    for flags in (0, 64, 4):
+        g.set_options(scenes.SolverOptions(**{**base, "flags": flags}))
+        out.append(g.vcycle(b))
+    g.close()
+    for u, its in out[1:]:
+        assert its == out[0][1]
+        assert np.array_equal(u, out[0][0])
 
 
 @pytest.mark.parametrize("name", ["bars_nh_cn", "cube8k_fcr", "cube_von_mises"])
