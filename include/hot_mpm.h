@@ -118,8 +118,11 @@ typedef struct {
                             bit 1: coarsest solve by the cooperative kernel, not the cluster one;
                             bit 2: one launch per Gauss-Seidel color on every level;
                             bit 3: one launch per color on the finest level only (by default
-                            each symmetric sweep of each level is one cooperative launch;
-                            bits 2 and 3 change launch boundaries only, not the arithmetic);
+                            each symmetric sweep of each level is one cooperative launch, or
+                            one 16-CTA cluster launch with hardware cluster barriers between
+                            colors on levels with at most 64 rows per color);
+                            bit 6: cooperative launches on those levels too (bits 2, 3 and 6
+                            change launch boundaries only, not the arithmetic);
                             bit 4: drive the L-BFGS iterations from the host;
                             bit 5: run them as one CUDA graph whose conditional nodes take every
                             decision on the device (by default the graph is used once the
