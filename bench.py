@@ -141,10 +141,13 @@ def algorithmic_units(name: str, stats_list, n_particles: int, precision: int):
     """Algorithmic work of kernel `name` summed over the timed steps.
 
     vcycle (the captured V-cycle of Alg. 2): per level m < M-1 four
-    Gauss-Seidel sweeps over the off-diagonal blocks and one residual over
-    all blocks.  FP64: 9 FMA = 18 flop per block visit (the FP64 pipe bounds
-    it).  FP32: 36 B of block values + 4 B column index per block visit (HBM
-    bounds it).  The coarsest PCG (latency bound, L2 resident) is not counted.
+    Gauss-Seidel sweeps over the off-diagonal blocks, of which the first
+    (forward, from u = 0) needs only the blocks of earlier-colored
+    neighbours -- exactly half of the off-diagonal blocks, since every
+    coupling joins two colors -- and one residual over all blocks.  FP64:
+    9 FMA = 18 flop per block visit (the FP64 pipe bounds it).  FP32: 36 B of
+    block values + 4 B column index per block visit (HBM bounds it).  The
+    coarsest PCG (latency bound, shared-memory resident) is not counted.
     hessian_cells: 27*27*3 + 378*9*3 FMA = 24,786 flop per particle."""
     if name == "hessian_cells":
         return 2 * (27 * 27 * 3 + 378 * 9 * 3) * n_particles * len(stats_list), "flop"
@@ -153,7 +156,7 @@ def algorithmic_units(name: str, stats_list, n_particles: int, precision: int):
         nl = st["n_levels"]
         for m in range(nl - 1):
             nnz, n = st["nnz_blocks"][m], st["n_nodes"][m]
-            visits += (4 * (nnz - n) + nnz) * st["vcycles"]
+            visits += ((7 * (nnz - n)) // 2 + nnz) * st["vcycles"]
     if precision == 0:
         return 18 * visits, "flop"
     return 40 * visits, "byte"

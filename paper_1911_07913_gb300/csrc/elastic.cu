@@ -290,7 +290,7 @@ template <class T>
 __global__ void __launch_bounds__(HNT) k_hessian_cells(const double *__restrict__ pd, int64_t np,
                                                       const T *__restrict__ A45, const int *__restrict__ cell_first,
                                                       const int *__restrict__ cell_n, const int *__restrict__ cell_key,
-                                                      G g, double dt, const int *__restrict__ map,
+                                                      G g, double dt2, const int *__restrict__ map,
                                                       const int *__restrict__ row_ptr,
                                                       const int *__restrict__ slotpos, T *__restrict__ vals) {
   __shared__ T sA[81];
@@ -331,23 +331,44 @@ __global__ void __launch_bounds__(HNT) k_hessian_cells(const double *__restrict_
     __syncthreads();
     if (threadIdx.x < 81) {
       int r = threadIdx.x / 9, cc = threadIdx.x % 9;
-      double sc = dt * dt * pd[PF_VOL * np + p];
-      sA[threadIdx.x] = (T)(sc * (double)A45[sym45(r, cc) * np + p]);
-    } else if (threadIdx.x >= 96 && threadIdx.x < 96 + 27) {
-      int k = threadIdx.x - 96;
-      int kx = k % 3, ky = (k / 3) % 3, kz = k / 9;
-      double fx[3], w[3][3], dw[3][3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        base_axis(pd[(PF_X + a) * np + p], g.o[a], g.inv_dx, &fx[a]);
-        bspline_axis<double>(fx[a], g.inv_dx, w[a], dw[a]);
+      const T sc = (T)(dt2 * pd[PF_VOL * np + p]);
+      sA[threadIdx.x] = sc * A45[sym45(r, cc) * np + p];
+    } else if (threadIdx.x >= 96 && threadIdx.x < 128) {
+      // one warp: lanes 0-8 evaluate the weights of (axis lane/3, node lane%3)
+      // and hold entry `lane` of F^n, then lanes 0-26 form node k's d = F^T grad w
+      // from shuffles.  In T: the FP32 Hessian takes FP32 weights (the base
+      // node stays exact in FP64).  FP64 instructions are scarce (2 FMA per
+      // clock per SM), so no lane repeats another's axis.
+      const int lane = threadIdx.x - 96;
+      T wv = T(0), dwv = T(0), Fv = T(0);
+      if (lane < 9) {
+        const int a = lane / 3, kk = lane % 3;
+        double fx;
+        base_axis(pd[(PF_X + a) * np + p], g.o[a], g.inv_dx, &fx);
+        T w[3], dw[3];
+        bspline_axis<T>((T)fx, (T)g.inv_dx, w, dw);
+        wv = kk == 0 ? w[0] : (kk == 1 ? w[1] : w[2]);
+        dwv = kk == 0 ? dw[0] : (kk == 1 ? dw[1] : dw[2]);
+        Fv = (T)pd[(PF_F + lane) * np + p];
       }
-      double gw[3] = {dw[0][kx] * w[1][ky] * w[2][kz], w[0][kx] * dw[1][ky] * w[2][kz],
-                      w[0][kx] * w[1][ky] * dw[2][kz]};
+      const int k = lane < 27 ? lane : 0;
+      const int kx = k % 3, ky = (k / 3) % 3, kz = k / 9;
+      const T wx = __shfl_sync(0xffffffffu, wv, kx), dwx = __shfl_sync(0xffffffffu, dwv, kx);
+      const T wy = __shfl_sync(0xffffffffu, wv, 3 + ky), dwy = __shfl_sync(0xffffffffu, dwv, 3 + ky);
+      const T wz = __shfl_sync(0xffffffffu, wv, 6 + kz), dwz = __shfl_sync(0xffffffffu, dwv, 6 + kz);
+      const T gw[3] = {dwx * wy * wz, wx * dwy * wz, wx * wy * dwz};
+      T d[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a)   // d_a = sum_b F_ba gw_b
-        sd[3 * k + a] = (T)(pd[(PF_F + a) * np + p] * gw[0] + pd[(PF_F + 3 + a) * np + p] * gw[1] +
-                            pd[(PF_F + 6 + a) * np + p] * gw[2]);
+      for (int b = 0; b < 3; ++b)     // d_a = sum_b F_ba gw_b, b in order
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const T Fba = __shfl_sync(0xffffffffu, Fv, 3 * b + a);
+          d[a] = b == 0 ? Fba * gw[0] : d[a] + Fba * gw[b];
+        }
+      if (lane < 27) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sd[3 * k + a] = d[a];
+      }
     }
     __syncthreads();
     for (int o = threadIdx.x; o < 27 * 27; o += HNT) {
@@ -521,7 +542,7 @@ void hessian_assemble(Scene &s, Hier<T> &h) {
   if (s.n_cells > 0) {
     ProfScope prof_(s, "hessian_cells");
     k_hessian_cells<T><<<(unsigned)s.n_cells, HNT, 0, s.st>>>(s.pd.p, s.np, h.A45.p, s.cell_first.p, s.cell_n.p,
-                                                             s.cell_key.p, geo(s), s.dt, t.map.p, t.row_ptr.p,
+                                                             s.cell_key.p, geo(s), s.dt * s.dt, t.map.p, t.row_ptr.p,
                                                              t.slotpos.p, L.vals.p);
     HOT_LAUNCH("k_hessian_cells");
   }

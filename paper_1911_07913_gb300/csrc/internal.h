@@ -34,22 +34,23 @@ struct Topo {
   DBuf<int> slotpos;         // 125 n: block position of (row, offset slot), -1 absent
   DBuf<uint32_t> mask;       // 4 n: present offset slots
   DBuf<int> rowcnt;          // n
+  DBuf<int> nlow;            // n: blocks of neighbours colored before the row (a prefix of the row)
   DBuf<int> color_list;      // n, grouped by color
   DBuf<int> color_cnt;       // 28
-  DBuf<int4> color_rec;      // n, (row, row_ptr[row], blocks in row, 0) in color_list order
+  DBuf<int4> color_rec;      // n, (row, row_ptr[row], blocks in row, nlow[row]) in color_list order
   int color_off[28] = {0};   // host copy of the per-color offsets
   void set_stream(cudaStream_t st) {
-    flag.st = st; map.st = coords.st = row_ptr.st = cols.st = slotpos.st = rowcnt.st = st;
+    flag.st = st; map.st = coords.st = row_ptr.st = cols.st = slotpos.st = rowcnt.st = nlow.st = st;
     mask.st = st; color_list.st = color_cnt.st = st; color_rec.st = st;
   }
   size_t bytes() const {
     return flag.bytes() + map.bytes() + coords.bytes() + row_ptr.bytes() + cols.bytes() +
-           slotpos.bytes() + mask.bytes() + rowcnt.bytes() + color_list.bytes() + color_cnt.bytes() +
+           slotpos.bytes() + mask.bytes() + rowcnt.bytes() + nlow.bytes() + color_list.bytes() + color_cnt.bytes() +
            color_rec.bytes();
   }
   void release() {
     flag.release(); map.release(); coords.release(); row_ptr.release(); cols.release();
-    slotpos.release(); mask.release(); rowcnt.release(); color_list.release(); color_cnt.release();
+    slotpos.release(); mask.release(); rowcnt.release(); nlow.release(); color_list.release(); color_cnt.release();
     color_rec.release();
   }
 };

@@ -81,31 +81,58 @@ __global__ void k_pattern0(int64_t n, const int *__restrict__ coords, const int 
 
 // cols / slotpos from the slot masks (columns in ascending slot order, which
 // is ascending node order for (z, y, x)-lexicographic numbering)
+// 27-coloring of the Gauss-Seidel sweeps: c = (x mod 3) + 3 (y mod 3) + 9 (z mod 3)
+__device__ __forceinline__ int node_color(int x, int y, int z) { return x % 3 + 3 * (y % 3) + 9 * (z % 3); }
+
+// cols / slotpos of each row from its offset mask.  A row keeps first the
+// blocks of neighbours colored before the row's own color, then the others
+// (the diagonal among them), each part in offset-slot order (which keeps
+// spatial neighbours adjacent for the gathers of u).  The first part, of
+// length nlow[i], is all that a Gauss-Seidel sweep starting from u = 0 needs
+// in its forward half: the other neighbours are still zero.  A stable
+// two-way partition with warp ballots; one warp per row.
 __global__ void k_fill_pattern(int64_t n, const int *__restrict__ coords, const int *__restrict__ map, Dims nd,
                                const uint32_t *__restrict__ mask, const int *__restrict__ row_ptr,
-                               int *__restrict__ cols, int *__restrict__ slotpos) {
+                               int *__restrict__ cols, int *__restrict__ slotpos, int *__restrict__ nlow) {
+  const int lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
-  int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  int ci[3] = {coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]};
-  int base = row_ptr[i];
-  int before = 0;
+  if (i >= n) return;   // warp-uniform
+  const int ci[3] = {coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]};
+  const int own = node_color(ci[0], ci[1], ci[2]);
+  unsigned lowb[4], highb[4];
+  int nlo = 0;
+#pragma unroll
   for (int r = 0; r < 4; ++r) {
-    uint32_t mk = mask[4 * i + r];
-    int s = r * 32 + lane;
-    bool on = (mk >> lane) & 1u;
-    int rank = before + __popc(mk & ((1u << lane) - 1u));
+    const int s = r * 32 + lane;
+    const bool on = s < NSLOT && ((mask[4 * i + r] >> lane) & 1u);
+    const int o[3] = {s % 5 - 2, (s / 5) % 5 - 2, s / 25 - 2};
+    const bool lo = on && node_color(ci[0] + o[0], ci[1] + o[1], ci[2] + o[2]) < own;
+    lowb[r] = __ballot_sync(0xffffffffu, lo);
+    highb[r] = __ballot_sync(0xffffffffu, on && !lo);
+    nlo += __popc(lowb[r]);
+  }
+  const int base = row_ptr[i];
+  const unsigned below = (1u << lane) - 1u;
+  int lo_before = 0, hi_before = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int s = r * 32 + lane;
     if (s < NSLOT) {
-      if (on) {
-        int o[3] = {s % 5 - 2, (s / 5) % 5 - 2, s / 25 - 2};
+      int rank = -1;
+      if ((lowb[r] >> lane) & 1u) rank = lo_before + __popc(lowb[r] & below);
+      else if ((highb[r] >> lane) & 1u) rank = nlo + hi_before + __popc(highb[r] & below);
+      if (rank >= 0) {
+        const int o[3] = {s % 5 - 2, (s / 5) % 5 - 2, s / 25 - 2};
         cols[base + rank] = map[lin(ci[0] + o[0], ci[1] + o[1], ci[2] + o[2], nd.d)];
         slotpos[i * NSLOT + s] = base + rank;
       } else {
         slotpos[i * NSLOT + s] = -1;
       }
     }
-    before += __popc(mk);
+    lo_before += __popc(lowb[r]);
+    hi_before += __popc(highb[r]);
   }
+  if (lane == 0) nlow[i] = nlo;
 }
 
 // coarse node candidates of every fine node: |a - 2A| <= 1 per axis
@@ -323,25 +350,25 @@ __global__ void k_diag(int64_t n, const int *__restrict__ row_ptr, const int *__
 __global__ void k_color_count(int64_t n, const int *__restrict__ coords, int *__restrict__ cnt) {
   int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (i >= n) return;
-  int c = coords[3 * i] % 3 + 3 * (coords[3 * i + 1] % 3) + 9 * (coords[3 * i + 2] % 3);
+  int c = node_color(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]);
   atomicAdd(&cnt[c], 1);
 }
 __global__ void k_color_fill(int64_t n, const int *__restrict__ coords, int *__restrict__ cursor,
                              int *__restrict__ list) {
   int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (i >= n) return;
-  int c = coords[3 * i] % 3 + 3 * (coords[3 * i + 1] % 3) + 9 * (coords[3 * i + 2] % 3);
+  int c = node_color(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]);
   list[atomicAdd(&cursor[c], 1)] = (int)i;
 }
 
 // one 16-byte record per entry of the color list: the row, where its blocks
 // start and how many there are (one load instead of a chain of three)
 __global__ void k_color_records(int64_t n, const int *__restrict__ list, const int *__restrict__ row_ptr,
-                                int4 *__restrict__ rec) {
+                                const int *__restrict__ nlow, int4 *__restrict__ rec) {
   int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (e >= n) return;
   const int i = list[e], rp = row_ptr[i];
-  rec[e] = make_int4(i, rp, row_ptr[i + 1] - rp, 0);
+  rec[e] = make_int4(i, rp, row_ptr[i + 1] - rp, nlow[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -430,17 +457,20 @@ struct RowRegs {
   T d[3];    // lanes 0-2: row `lane` of D_i^-1
 };
 
+// nb: blocks in the row (the stride of its entry streams); nuse: the leading
+// blocks to use (nb, or the prefix of neighbours colored before the row when
+// the others are still zero)
 template <class T>
-__device__ __forceinline__ void load_row(RowRegs<T> &R, int64_t i, int rp, int nb, int lane,
+__device__ __forceinline__ void load_row(RowRegs<T> &R, int64_t i, int rp, int nb, int nuse, int lane,
                                          const int *__restrict__ cols, const T *__restrict__ vals,
                                          const T *__restrict__ dinv, const T *__restrict__ b) {
   const T *v = vals + 9 * (int64_t)rp;
 #pragma unroll
   for (int q = 0; q < SW_PRE; ++q) {
     const int e0 = lane + 32 * q;
-    R.j[q] = e0 < nb ? cols[rp + e0] : -1;
+    R.j[q] = e0 < nuse ? cols[rp + e0] : -1;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) R.h[q][e] = e0 < nb ? v[e * nb + e0] : T(0);
+    for (int e = 0; e < 9; ++e) R.h[q][e] = e0 < nuse ? v[e * nb + e0] : T(0);
   }
   R.bv = ((lane & 7) == 0 && lane < 24) ? b[3 * i + (lane >> 3)] : T(0);
 #pragma unroll
@@ -456,7 +486,7 @@ __device__ __forceinline__ T ld_u(const T *p) {
 }
 
 template <class T, bool LDCG = true>
-__device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int rp, int nb, int lane,
+__device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int rp, int nb, int nuse, int lane,
                                            const int *__restrict__ cols, const T *__restrict__ vals, T *u) {
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -476,7 +506,7 @@ __device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int r
   }
   // rows longer than the register window (not produced by the 5^3 stencil)
   const T *v = vals + 9 * (int64_t)rp;
-  for (int e0 = lane + 32 * SW_PRE; e0 < nb; e0 += 32) {
+  for (int e0 = lane + 32 * SW_PRE; e0 < nuse; e0 += 32) {
     const int j = cols[rp + e0];
     if (j == i) continue;
     const T u0 = ld_u<T, LDCG>(u + 3 * j), u1 = ld_u<T, LDCG>(u + 3 * j + 1), u2 = ld_u<T, LDCG>(u + 3 * j + 2);
@@ -501,16 +531,19 @@ __device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int r
 // (one warp per row; lanes 0, 8, 16 form the three residual components and
 // lanes 0-2 apply the three rows of D_i^{-1}).
 // one color of a sweep, one launch (rows given by their color records)
+// (low: only the prefix of neighbours colored before the row, r.w blocks)
 template <class T>
 __global__ void k_sgs_color(const int4 *__restrict__ rec, int nrows, const int *__restrict__ cols,
-                            const T *__restrict__ vals, const T *__restrict__ dinv, const T *__restrict__ b, T *u) {
+                            const T *__restrict__ vals, const T *__restrict__ dinv, const T *__restrict__ b, T *u,
+                            int low) {
   const int g = blockIdx.x * WPB + (threadIdx.x >> 5);
   if (g >= nrows) return;   // warp-uniform
   const int lane = threadIdx.x & 31;
   const int4 r = rec[g];
+  const int nuse = low ? r.w : r.z;
   RowRegs<T> R;
-  load_row<T>(R, r.x, r.y, r.z, lane, cols, vals, dinv, b);
-  update_row<T, false>(R, r.x, r.y, r.z, lane, cols, vals, u);
+  load_row<T>(R, r.x, r.y, r.z, nuse, lane, cols, vals, dinv, b);
+  update_row<T, false>(R, r.x, r.y, r.z, nuse, lane, cols, vals, u);
 }
 
 // r = b - H u
@@ -692,6 +725,7 @@ struct SweepPlan {
   int off[54];   // first entry of each step's rows in the color list
   int nr[54];    // rows of each step
   int steps;
+  int low_steps; // leading steps whose rows use only their lower-colored prefix (sweep from u = 0)
 };
 
 constexpr int SW_NT = 512;
@@ -720,26 +754,32 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, con
   __shared__ int s_ok;
   const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int first = blockIdx.x + G * warp;   // this warp's first-round row of every step
-  for (int k = lane; k < plan.steps; k += 32)
-    s_rec[k][warp] = first < plan.nr[k] ? rec[plan.off[k] + first] : make_int4(-1, 0, 0, 0);
+  // .w becomes the number of leading blocks this step uses (the earlier-colored
+  // prefix while u is zero beyond it, else the whole row)
+  for (int k = lane; k < plan.steps; k += 32) {
+    int4 rr = first < plan.nr[k] ? rec[plan.off[k] + first] : make_int4(-1, 0, 0, 0);
+    if (k >= plan.low_steps) rr.w = rr.z;
+    s_rec[k][warp] = rr;
+  }
   if (threadIdx.x == 0) s_ok = 1;
   __syncthreads();
   RowRegs<T> R;
   {
     const int4 r0 = s_rec[0][warp];
-    if (r0.x >= 0) load_row<T>(R, r0.x, r0.y, r0.z, lane, cols, vals, dinv, b);
+    if (r0.x >= 0) load_row<T>(R, r0.x, r0.y, r0.z, r0.w, lane, cols, vals, dinv, b);
   }
   unsigned target = 0;
   for (int k = 0; k < plan.steps; ++k) {
     const int4 r = s_rec[k][warp];
-    if (r.x >= 0) update_row<T, true>(R, r.x, r.y, r.z, lane, cols, vals, u);
+    if (r.x >= 0) update_row<T, true>(R, r.x, r.y, r.z, r.w, lane, cols, vals, u);
     // further rounds (more rows in this color than warps in the grid)
     if (MULTI) {
       for (int g = first + G * SW_WARPS; g < plan.nr[k]; g += G * SW_WARPS) {
         const int4 r2 = rec[plan.off[k] + g];
+        const int nuse2 = k < plan.low_steps ? r2.w : r2.z;
         RowRegs<T> R2;
-        load_row<T>(R2, r2.x, r2.y, r2.z, lane, cols, vals, dinv, b);
-        update_row<T, true>(R2, r2.x, r2.y, r2.z, lane, cols, vals, u);
+        load_row<T>(R2, r2.x, r2.y, r2.z, nuse2, lane, cols, vals, dinv, b);
+        update_row<T, true>(R2, r2.x, r2.y, r2.z, nuse2, lane, cols, vals, u);
       }
     }
     if (k + 1 == plan.steps) break;
@@ -748,7 +788,7 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, con
       __syncwarp();
       asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
       const int4 rn = s_rec[k + 1][warp];
-      if (rn.x >= 0) load_row<T>(R, rn.x, rn.y, rn.z, lane, cols, vals, dinv, b);
+      if (rn.x >= 0) load_row<T>(R, rn.x, rn.y, rn.z, rn.w, lane, cols, vals, dinv, b);
       asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
       continue;
     }
@@ -756,7 +796,7 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, con
     if (threadIdx.x == 0) bar_arrive_release(bar);
     target += (unsigned)G;
     const int4 rn = s_rec[k + 1][warp];
-    if (rn.x >= 0) load_row<T>(R, rn.x, rn.y, rn.z, lane, cols, vals, dinv, b);
+    if (rn.x >= 0) load_row<T>(R, rn.x, rn.y, rn.z, rn.w, lane, cols, vals, dinv, b);
     if (threadIdx.x == 0) {
       long long spins = 0;
       while (bar_load_acquire(bar) < target) {
@@ -1054,6 +1094,7 @@ void build_pattern0(Scene &s) {
   const int64_t n = t.n;
   t.mask.ensure(4 * (size_t)n + 4);
   t.rowcnt.ensure(n + 1);
+  t.nlow.ensure(n + 1);
   t.row_ptr.ensure(n + 1);
   t.slotpos.ensure((size_t)NSLOT * n + NSLOT);
   if (n == 0) {
@@ -1070,7 +1111,7 @@ void build_pattern0(Scene &s) {
   t.nnzb = read_scan_total(s.scan, s.st);
   t.cols.ensure(t.nnzb);
   k_fill_pattern<<<nbw, NT, 0, s.st>>>(n, t.coords.p, t.map.p, dims_of(t), t.mask.p, t.row_ptr.p, t.cols.p,
-                                       t.slotpos.p);
+                                       t.slotpos.p, t.nlow.p);
   HOT_LAUNCH("k_fill_pattern");
 }
 
@@ -1090,6 +1131,7 @@ void build_coarse_topology(Scene &s, int m) {
   const int64_t n = C.n;
   C.mask.ensure(4 * (size_t)n + 4);
   C.rowcnt.ensure(n + 1);
+  C.nlow.ensure(n + 1);
   C.row_ptr.ensure(n + 1);
   C.slotpos.ensure((size_t)NSLOT * n + NSLOT);
   if (n == 0) {
@@ -1105,7 +1147,7 @@ void build_coarse_topology(Scene &s, int m) {
   C.nnzb = read_scan_total(s.scan, s.st);
   C.cols.ensure(C.nnzb);
   k_fill_pattern<<<nbw, NT, 0, s.st>>>(n, C.coords.p, C.map.p, dims_of(C), C.mask.p, C.row_ptr.p, C.cols.p,
-                                       C.slotpos.p);
+                                       C.slotpos.p, C.nlow.p);
   HOT_LAUNCH("k_fill_pattern");
 }
 
@@ -1130,7 +1172,7 @@ void build_colors(Scene &s, int m) {
   HOT_CUDA(cudaMemcpyAsync(t.color_cnt.p, t.color_off, sizeof(int) * 27, cudaMemcpyHostToDevice, s.st));
   k_color_fill<<<nb, NT, 0, s.st>>>(t.n, t.coords.p, t.color_cnt.p, t.color_list.p);
   HOT_LAUNCH("k_color_fill");
-  k_color_records<<<nb, NT, 0, s.st>>>(t.n, t.color_list.p, t.row_ptr.p, t.color_rec.p);
+  k_color_records<<<nb, NT, 0, s.st>>>(t.n, t.color_list.p, t.row_ptr.p, t.nlow.p, t.color_rec.p);
   HOT_LAUNCH("k_color_records");
   HOT_CUDA(cudaStreamSynchronize(s.st));   // color_off (host) must outlive the async copy
 }
@@ -1281,11 +1323,16 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
 // cooperative launch (one cluster launch on levels whose colors fit a
 // cluster's warps); flag bit 2 makes it one launch per color on every
 // level, bit 3 on the finest level only.
+// from_zero: u = 0 on entry (pre-smoothing), so in the forward half a row's
+// neighbours of later colors are still zero and only its prefix of earlier-
+// colored neighbours is read; the skipped terms are exact zeros, so the result
+// is bitwise that of the full rows.
 template <class T>
-void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
+void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m, bool from_zero) {
   ProfScope sweep_(s, SWEEP_SCOPE[m & 7]);
   SweepPlan plan;
   plan.steps = 0;
+  plan.low_steps = 0;
   int max_rows = 0;
   bool skipped = false;
   for (int k = 0; k < 54; ++k) {
@@ -1300,6 +1347,7 @@ void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
     plan.off[plan.steps] = t.color_off[c];
     plan.nr[plan.steps] = nr;
     plan.steps += 1;
+    if (forward && from_zero) plan.low_steps = plan.steps;
     max_rows = std::max(max_rows, nr);
   }
   if (plan.steps == 0) return;
@@ -1312,7 +1360,8 @@ void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m) {
   for (int k = 0; k < plan.steps; ++k) {
     ProfScope prof_(s, "sgs");
     k_sgs_color<T><<<(unsigned)((plan.nr[k] + WPB - 1) / WPB), NT, 0, s.st>>>(
-        t.color_rec.p + plan.off[k], plan.nr[k], t.cols.p, V.vals.p, V.dinv.p, V.b.p, V.u.p);
+        t.color_rec.p + plan.off[k], plan.nr[k], t.cols.p, V.vals.p, V.dinv.p, V.b.p, V.u.p,
+        k < plan.low_steps ? 1 : 0);
     HOT_LAUNCH("k_sgs_color");
   }
 }
@@ -1452,7 +1501,7 @@ void vcycle_launches(Scene &s, Hier<T> &h, const double *b_in, double *u_out) {
     Topo &t = s.topo[m];
     Vals<T> &V = h.L[m];
     HOT_CUDA(cudaMemsetAsync(V.u.p, 0, sizeof(T) * 3 * t.n, s.st));
-    sgs_symmetric<T>(s, t, V, h, m);
+    sgs_symmetric<T>(s, t, V, h, m, true);
     {
       ProfScope prof_(s, "residual");
       k_residual<T><<<(unsigned)((t.n + WPB - 1) / WPB), NT, 0, s.st>>>(
@@ -1472,7 +1521,7 @@ void vcycle_launches(Scene &s, Hier<T> &h, const double *b_in, double *u_out) {
     k_prolong_add<T><<<(unsigned)((t.n + NT - 1) / NT), NT, 0, s.st>>>(t.n, t.coords.p, c.map.p, dims_of(c),
                                                                        h.L[m + 1].u.p, V.u.p);
     HOT_LAUNCH("k_prolong_add");
-    sgs_symmetric<T>(s, t, V, h, m);
+    sgs_symmetric<T>(s, t, V, h, m, false);
   }
   k_store_out<T><<<(unsigned)((3 * t0.n + NT - 1) / NT), NT, 0, s.st>>>(t0.n, h.L[0].u.p, s.fixed.p, u_out);
   HOT_LAUNCH("k_store_out");
