@@ -366,6 +366,40 @@ def test_rap_matches_dense_triple_product_and_full_rank():
         assert np.abs(off).max() <= 2
 
 
+def test_colors_uncoupled_and_zero_start_forward_sweep_uses_earlier_colors_only():
+    """The 27-coloring: no block couples two nodes of one color (couplings
+    reach offset 2, colors repeat every 3), so the blocks of earlier-colored
+    neighbours are exactly half of the off-diagonal blocks of the symmetric
+    pattern.  From u = 0, a forward sweep equals the substitution that uses
+    only those blocks: the later-colored neighbours are still zero when a
+    row is updated."""
+    sc = free_scene(9, F_jitter=0.2)
+    g, prob, L = hierarchy_for(sc)
+    rng = np.random.default_rng(9)
+    for lev in L:
+        n = lev.coords.shape[0]
+        col = np.zeros(n, int)
+        for c, rows in enumerate(lev.colors):
+            col[rows] = c
+        P = lev.pattern.tocoo()
+        off = P.row != P.col
+        assert np.all(col[P.row[off]] != col[P.col[off]])
+        assert (lev.pattern != lev.pattern.T).nnz == 0
+        nnz, earlier = P.nnz, int(np.sum(col[P.col] < col[P.row]))
+        assert 2 * earlier == nnz - n
+        b = rng.normal(size=(n, 3))
+        u_sweep = O.sgs(lev, np.zeros((n, 3)), b, forward=True)
+        H = lev.H.toarray().reshape(n, 3, n, 3)
+        u = np.zeros((n, 3))
+        for c in range(27):
+            for i in lev.colors[c]:
+                js = np.nonzero(col < c)[0]
+                # H[i, :, js, :] has shape (len(js), 3, 3): the index array's axis comes first
+                rhs = b[i] - np.einsum("jab,jb->a", H[i, :, js, :], u[js]) if js.size else b[i].copy()
+                u[i] = np.linalg.solve(lev.Dblk[i], rhs)
+        np.testing.assert_allclose(u, u_sweep, rtol=1e-12, atol=1e-12 * np.abs(u_sweep).max())
+
+
 def test_galerkin_force_identity():
     """R f^0 equals the force computed with the embedded weight gradients
     sum_i R_ji grad w_ip (Sec. 4.2)."""
