@@ -2,6 +2,7 @@
 itself -- closed forms, invariants, finite differences, brute-force dense
 algebra and the paper's stated settings -- so that a dropped term, a wrong
 sign or index, or a transposed operand fails at least one of them."""
+import copy
 import json
 import os
 
@@ -501,6 +502,43 @@ def test_hot_matches_dense_newton_on_tiny_grid(model):
     np.testing.assert_allclose(dv, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
     # line-search invariant: accepted energies never increase
     assert np.all(np.diff(tr.energies) <= 0)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_minimiser_is_equivariant_under_a_grid_rotation(model):
+    """A quarter turn about z through a grid node of the domain's centre maps
+    the grid, the stencils and the held wall layers onto themselves.  The
+    incremental potential of the rotated scene (x' = c + Q(x - c), v' = Qv,
+    F' = QFQ^T, C' = QCQ^T, g' = Qg) is that of the original seen in the
+    rotated frame, so its minimiser is the rotated minimiser:
+    dv'(c + Q(x_i - c)) = Q dv(x_i).  An axis or index transposed anywhere
+    in P2G, the energy or the gradient breaks this."""
+    sc = scenes.tiny_scene(seed=21, res=16, cells=(2, 1, 1), lo=(6, 6, 7), ppc_axis=2,
+                           model=model, E=1e4, F_jitter=0.1, gravity=(1.0, -9.8, 0.5))
+    Q = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    c = np.full(3, 8 * sc.dx)
+    rot = copy.deepcopy(sc)
+    rot.x = c + (sc.x - c) @ Q.T
+    rot.v = sc.v @ Q.T
+    rot.F = Q @ sc.F @ Q.T
+    rot.C = Q @ sc.C @ Q.T
+    rot.gravity = Q @ sc.gravity
+    out = []
+    for s_ in (sc, rot):
+        g = O.p2g(s_)
+        prob = O.Problem(s_, g, 2e-2)
+        out.append((g, dense_newton(prob)))
+    (g0, dv0), (g1, dv1) = out
+    assert g0.coords.shape == g1.coords.shape
+    k = np.rint((g0.pos - c) @ Q.T / sc.dx).astype(np.int64) + 8
+    index1 = {tuple(t): i for i, t in enumerate(g1.coords.tolist())}
+    perm = np.array([index1[tuple(t)] for t in k.tolist()])
+    np.testing.assert_array_equal(g1.fixed[perm], g0.fixed)
+    np.testing.assert_allclose(g1.m[perm], g0.m, rtol=1e-13)
+    # 1e-8: the FCR stress goes through the oracle's polar decomposition, whose
+    # rounding leaves Newton's minimiser ~1e-9 relative from exact; a transposed
+    # axis or index would show as an O(1) difference
+    np.testing.assert_allclose(dv1[perm], dv0 @ Q.T, rtol=0, atol=1e-8 * np.abs(dv0).max())
 
 
 def test_free_fall_gets_gravity_increment():
