@@ -109,7 +109,8 @@ typedef struct {
                             coarse solve, FP64 energy/gradient/L-BFGS/CN */
   int32_t max_iters;     /* L-BFGS iteration cap */
   int32_t max_ls;        /* line-search halvings cap */
-  int32_t max_coarse_cg; /* coarsest-level PCG cap; 0 = number of coarse DOFs */
+  int32_t max_coarse_cg; /* coarsest-level PCG cap; 0 = number of coarse DOFs, at most 100 when
+                            the V-cycle runs in FP32 (precision 1) */
   int32_t record_trace;  /* 1: keep the decision trace (mpm_get_trace) */
   double dt;             /* > 0: fixed step; else min(1/fps, cfl dx / v_max) */
   double fps;
