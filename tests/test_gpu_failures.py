@@ -1,0 +1,93 @@
+"""Error paths of the C ABI, driven from the host (no GPU fault, trap or
+hang): a failing device allocator, a NaN in the particle input, and the
+L-BFGS iteration cap.  Each call returns its status and leaves the library
+usable."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_1911_07913_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hot():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1911_07913_gb300 import hot as H
+    H.load()
+    return H
+
+
+def small_cube():
+    sc = scenes.cube_scene(seed=5, res=16, cube_lo=(5, 4, 5), side=4)
+    return sc, scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=4e-3, levels=2)
+
+
+def test_allocation_failure_is_reported_and_recoverable(hot):
+    """An allocator that fails from its fourth request on: scene creation
+    returns MPM_ERR_OOM and frees what it had taken; with the normal
+    allocator back, a scene steps as usual."""
+    import torch
+    lib = hot.load()
+    sc, opts = small_cube()
+    calls = {"n": 0}
+    live = set()   # pointers this allocator handed out and the library has not freed
+
+    def _alloc(nbytes, stream, ctx):
+        calls["n"] += 1
+        if calls["n"] >= 4:
+            return None
+        ptr = int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0))
+        live.add(ptr)
+        return ptr
+
+    def _free(ptr, stream, ctx):
+        live.discard(int(ptr))
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = hot.ALLOC_FN(_alloc), hot.FREE_FN(_free)
+    assert lib.mpm_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), None) == 0
+    try:
+        with pytest.raises(hot.HotError) as err:
+            hot.HotScene(sc, opts)
+        assert err.value.code == 2          # MPM_ERR_OOM
+        assert calls["n"] == 4 and not live
+    finally:
+        hot._install_torch_allocator(lib)
+    g = hot.HotScene(sc, opts)
+    st = g.step()
+    assert st["status"] == 0 and st["iters"] >= 1
+    g.close()
+
+
+def test_nan_input_reports_numeric(hot):
+    """A NaN velocity reaches the gradient; the convergence test reports
+    MPM_ERR_NUMERIC and G2P is not applied."""
+    sc, opts = small_cube()
+    sc.v[7, 1] = np.nan
+    g = hot.HotScene(sc, opts)
+    x0 = g.get_state()["x"].copy()
+    st = g.step(check=False)
+    assert st["code"] == 6                  # MPM_ERR_NUMERIC
+    np.testing.assert_array_equal(g.get_state()["x"], x0)
+    g.close()
+
+
+def test_iteration_cap_reports_not_converged_and_advances(hot):
+    """With max_iters = 2 and a tolerance no two iterations reach, the step
+    returns MPM_ERR_NOT_CONVERGED after exactly two iterations and G2P
+    applies the last accepted iterate."""
+    sc, opts = small_cube()
+    opts = scenes.SolverOptions(**{**opts.__dict__, "eps": 1e-13, "max_iters": 2})
+    g = hot.HotScene(sc, opts)
+    x0 = g.get_state()["x"].copy()
+    st = g.step(check=False)
+    assert st["code"] == 4                  # MPM_ERR_NOT_CONVERGED
+    assert st["iters"] == 2
+    x1 = g.get_state()["x"]
+    assert np.all(np.isfinite(x1)) and not np.array_equal(x1, x0)
+    g.close()
