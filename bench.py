@@ -1,14 +1,19 @@
 #!/usr/bin/env python
-"""Throughput of the HOT implicit MPM step on GB300: particle-steps/s.
+"""Throughput of the HOT implicit MPM step on GB300: particle-steps/s at a
+fixed residual tolerance.
 
 Default workload: two twisted bars, 601,600 particles on a sparse 256^3 grid
 (dx = 1/256), Neo-Hookean E = 1e5 / 1e9 Pa, nu = 0.4, rho = 2000, ends
 rotating at +-1 rad/s, dt at CFL 0.6 (24 FPS cap), 5-level multigrid, FP64,
-characteristic-norm tolerance eps = 1e-7.  A step is one full implicit step
-(P2G, HOT solve, G2P) on device-resident particles.  Also reported: the same
-metric end to end through the C ABI with host buffers, the mixed-precision
-form on the 2M-particle version of the scene, the dominant kernel against its
-roofline, p50/p99 step latency, and the FP64 oracle on the host cores.
+characteristic-norm tolerance eps = 1e-7 (Sec. 5.2, Sec. 6.1).  A step is one
+full implicit step (P2G, HOT solve, G2P) on device-resident particles.  Only
+steps whose solve met the tolerance earn particle-steps; every step's status,
+iteration count and final norm is printed.  Also reported: the same metric
+end to end through the C ABI with host buffers, the mixed-precision form
+against FP64 on the same scenes (600k and 2M particles) with its per-step
+error, the dominant kernel against its roofline, p50/p99 step latency, batched
+and served stepping, the paper's comparison solvers, and the FP64 oracle on
+the host cores (one core and all cores).
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -38,14 +43,22 @@ from paper_1911_07913_gb300 import scenes  # noqa: E402
 METRIC = "particle-steps/s at fixed residual tol (HOT implicit MPM step)"
 UNIT = "particle-steps/s"
 
-# measured FP64 FMA throughput unit count: 2 FP64 FMA per SM per clock on
-# GB300 -> 152 SMs x 4 flop x 2.07 GHz
+# FP64 pipe of GB300: 2 FP64 FMA per SM per clock -> 152 SMs x 4 flop x 2.07
+# GHz = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s); bench.py also measures it
+# live with the library's FMA probe and reports both.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
+# Every timed configuration rebuilds the projected Hessian and its hierarchy
+# at the current iterate every REFRESH iterations of an unconverged solve (an
+# extension of Alg. 3, which builds it once per step): with the hierarchy of
+# dv = 0 alone, L-BFGS stalls on steps whose Hessian changes strongly within
+# the step (measured on these scenes; the comparison is in the design notes).
+REFRESH = 5
 
-def workload_opts(precision: int) -> scenes.SolverOptions:
+
+def workload_opts(precision: int, refresh: int = REFRESH) -> scenes.SolverOptions:
     return scenes.SolverOptions(eps=1e-7, cn_mode=0, lbfgs_m=8, levels=5, precision=precision,
-                                max_iters=500)
+                                max_iters=500, refresh_every=refresh)
 
 
 def workload_desc(sc, opts, extra=None):
@@ -56,7 +69,12 @@ def workload_desc(sc, opts, extra=None):
                 f"ends at +-1 rad/s, sparse {int(sc.grid_dims[0])}^3 grid")
     d = {"workload": what,
          "particles": sc.n, "dx": sc.dx, "levels": opts.levels, "lbfgs_window": opts.lbfgs_m,
-         "tolerance": f"CN eps={opts.eps}", "dt": "min(1/24, 0.6 dx / v_max)",
+         "tolerance": f"CN eps={opts.eps}" if opts.cn_mode == 0 else f"||g|| <= {opts.eps} ||g1||",
+         "dt": "min(1/24, 0.6 dx / v_max)" if opts.dt <= 0 else opts.dt,
+         "solver": ("HOT: L-BFGS (Alg. 3) preconditioned by the Galerkin V-cycle (Alg. 2)"
+                    + (f", hierarchy rebuilt at the iterate every {opts.refresh_every} iterations"
+                       if opts.refresh_every else "")),
+         "max_iters": opts.max_iters,
          "precision": "fp64" if opts.precision == 0 else "mixed (fp32 Hessian/V-cycle, fp64 E/grad/L-BFGS/CN)",
          "l2": "inputs larger than L2 (particles + Hessian > 129 MB)"}
     if extra:
@@ -178,7 +196,7 @@ def vcycle_traffic(key):
     return float(v) if v else None
 
 
-def roofline_entry(name, prof, stats_list, n_particles, precision, peaks, traffic_key=None):
+def roofline_entry(name, prof, stats_list, n_particles, precision, peaks, traffic_key=None, fp64_probe=None):
     """Dominant-kernel roofline from live CUDA-event times over the timed steps."""
     p = prof.get(name)
     if not p or p["launches"] == 0:
@@ -191,9 +209,13 @@ def roofline_entry(name, prof, stats_list, n_particles, precision, peaks, traffi
             "timed": "CUDA events around every V-cycle, over a replay of the timed steps from their start state"}
     if kind == "flop":
         achieved = units / secs / 1e12
-        return {**base, "bound": "alu", "achieved": achieved, "peak": round(FP64_PEAK_TFLOPS, 3),
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (probe: 1.20 TFLOP/s at 1995 MHz)"}
+        out = {**base, "bound": "alu", "achieved": achieved, "peak": round(FP64_PEAK_TFLOPS, 3),
+               "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+               "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+        if fp64_probe:
+            out["fp64_probe_tflops"] = fp64_probe
+            out["frac_of_probe"] = achieved / fp64_probe
+        return out
     achieved = units / secs / 1e9
     hbm = peaks.get("hbm_gbs", 6800.0)
     return {**base, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -208,59 +230,138 @@ def load_peaks():
 
 
 # --------------------------------------------------------------------------- our arm
-def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, rank, local, sample_clocks=True, profile_run=False):
-    """Warm-up, one profiled breakdown step, K timed steps (the L-BFGS loop as
-    one device-driven CUDA graph, no profiling), then the same K steps replayed
-    from the same state with CUDA events around every V-cycle (`dominant`) for
-    the roofline, and the end-to-end pass through host buffers."""
+def step_record(stats, step_ms=None):
+    """Per-step status of a run: iterations, mpm_status, final termination
+    norm, dt (and device time); `converged` counts the steps whose solve met
+    the tolerance (status 0)."""
+    rec = {"iters": [int(s["iters"]) for s in stats], "status": [int(s["status"]) for s in stats],
+           "cn_norm": [float("%.4g" % s["final_norm"]) for s in stats],
+           "dt": [float("%.5g" % s["dt"]) for s in stats]}
+    if step_ms is not None:
+        rec["ms"] = [round(float(x), 3) for x in step_ms]
+    rec["converged"] = sum(1 for s in stats if int(s["status"]) == 0)
+    rec["steps"] = len(stats)
+    return rec
+
+
+def credited_rate(n_particles: int, stats, total_ms: float, ws: int = 1) -> float:
+    """Particle-steps/s counting only the steps that met the tolerance, over
+    the time of all steps: an unconverged step costs time and earns nothing."""
+    conv = sum(1 for s in stats if int(s["status"]) == 0)
+    return n_particles * ws * conv / (total_ms / 1e3)
+
+
+def timed_steps(g, steps, stream):
+    """K steps of scene g between CUDA events on its stream."""
     import torch
-    from paper_1911_07913_gb300 import hot
-    torch.cuda.set_device(local)
-    stream = torch.cuda.Stream()
-    g = hot.HotScene(sc, opts, stream=stream.cuda_stream)
-    for _ in range(warmup):
-        g.step(check=False)
-    breakdown = {}
-    if warmup > 0 and not profile_run:
-        # full kernel breakdown on one extra untimed step
-        g.profile(True)
-        g.step()
-        breakdown = g.profile_read()
-        g.profile(False)
-    start_state = g.get_state()
-    stats = []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    launches0 = hot.kernel_launch_count()
-    if sample_clocks:
-        clocks.start()
+    stats = []
     torch.cuda.synchronize()
     ev[0].record(stream)
     for k in range(steps):
         stats.append(g.step(check=False))
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop() if sample_clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (profiling run)"]}
+    return stats, [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)], ev[0].elapsed_time(ev[steps])
+
+
+def grid_velocity(g):
+    """Node coordinates and v^{n+1} = v^n + dv of the last solved step."""
+    gr = g.grid()
+    return gr["coords"], gr["v"] + gr["dv"]
+
+
+def mixed_error(c64, v64, x64, c32, v32, x32, x_prev, dx):
+    """Error of a mixed-precision step against the FP64 step from the same
+    state: grid v^{n+1} (relative infinity norm over the nodes) and particle
+    positions (relative to |x|, in cells, and relative to the step's
+    displacement)."""
+    if c64.shape != c32.shape or not np.array_equal(c64, c32):
+        return {"grid_v_rel": None, "x_rel": None, "note": "node sets differ"}
+    dvx = np.abs(x32 - x64).max()
+    disp = np.abs(x64 - x_prev).max()
+    return {"grid_v_rel": float(np.abs(v32 - v64).max() / max(np.abs(v64).max(), 1e-300)),
+            "x_rel": float(dvx / np.abs(x64).max()), "x_cells": float(dvx / dx),
+            "x_rel_to_step_displacement": float(dvx / max(disp, 1e-300))}
+
+
+def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, local, sample_clocks=True, profile_run=False,
+            partner_opts=None, fp64_probe=None):
+    """Warm-up, one profiled breakdown step, K timed steps (the L-BFGS loop on
+    the device), the same K steps of the partner precision from the same start
+    state (timed alike), then a replay of the K steps with CUDA events around
+    every V-cycle (`dominant`) for the roofline, in which the partner also
+    steps from each FP64 state so that its per-step error is measured, and the
+    end-to-end pass through host buffers."""
+    import torch
+    from paper_1911_07913_gb300 import hot
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    g = hot.HotScene(sc, opts, stream=stream.cuda_stream)
+    warm = [g.step(check=False) for _ in range(warmup)]
+    breakdown = {}
+    if warmup > 0 and not profile_run:
+        g.profile(True)
+        g.step(check=False)
+        breakdown = g.profile_read()
+        g.profile(False)
+    start_state = g.get_state()
+    clocks = ClockSampler(local)
+    launches0 = hot.kernel_launch_count()
+    if sample_clocks:
+        clocks.start()
+    stats, step_ms, total_ms = timed_steps(g, steps, stream)
+    clk = clocks.stop() if sample_clocks else {"sm_mhz": None, "sm_max_mhz": None,
+                                                 "reasons": ["not sampled (profiling run)"]}
     launches = hot.kernel_launch_count() - launches0
-    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
-    total_ms = ev[0].elapsed_time(ev[steps])
-    # roofline: the same steps again, every V-cycle between CUDA events
-    prof, prof_stats = {}, []
+    out = {"total_ms": total_ms, "step_ms": step_ms, "stats": stats, "warm": warm, "breakdown": breakdown,
+           "clocks": clk, "launches": launches, "device_loop": all(st.get("device_loop", 0) == 1 for st in stats)}
+    g2 = None
+    if partner_opts is not None:
+        stream2 = torch.cuda.Stream()
+        g2 = hot.HotScene(sc, partner_opts, stream=stream2.cuda_stream)
+        replay_state(g2, sc, start_state)
+        clocks2 = ClockSampler(local)
+        clocks2.start()
+        st2, ms2, tot2 = timed_steps(g2, steps, stream2)
+        out["partner"] = {"stats": st2, "step_ms": ms2, "total_ms": tot2, "clocks": clocks2.stop()}
+        g2.profile(True)
+        g2.step(check=False)
+        out["partner"]["breakdown"] = g2.profile_read()
+        g2.profile(False)
     if not profile_run:
         replay_state(g, sc, start_state)
         g.profile(True, only=dominant)
-        prof_stats = [g.step(check=False) for _ in range(steps)]
+        if g2 is not None:
+            g2.profile(True, only="vcycle")
+        prof_stats, errors, partner_stats = [], [], []
+        for k in range(steps):
+            s_k = g.get_state() if g2 is not None else None
+            prof_stats.append(g.step(check=False))
+            if g2 is not None:
+                c64, v64 = grid_velocity(g)
+                x64 = g.get_state()["x"]
+                replay_state(g2, sc, s_k)
+                partner_stats.append(g2.step(check=False))
+                c32, v32 = grid_velocity(g2)
+                x32 = g2.get_state()["x"]
+                errors.append(mixed_error(c64, v64, x64, c32, v32, x32, s_k["x"], sc.dx))
         torch.cuda.synchronize()
-        prof = g.profile_read()
+        out["prof"] = g.profile_read()
+        out["prof_stats"] = prof_stats
         g.profile(False)
-    e2e = None
-    if with_e2e:
-        e2e = run_e2e(g, sc, steps, stream, start_state)
+        if g2 is not None:
+            out["partner"]["prof"] = g2.profile_read()
+            out["partner"]["prof_stats"] = partner_stats
+            out["partner"]["errors"] = errors
+            g2.profile(False)
+    else:
+        out["prof"], out["prof_stats"] = {}, []
+    if g2 is not None:
+        g2.close()
+    out["e2e"] = run_e2e(g, sc, steps, stream, start_state) if with_e2e else None
     g.close()
-    return {"total_ms": total_ms, "step_ms": step_ms, "stats": stats, "prof": prof, "prof_stats": prof_stats,
-            "breakdown": breakdown, "clocks": clk, "launches": launches, "e2e": e2e,
-            "device_loop": all(st.get("device_loop", 0) == 1 for st in stats)}
+    return out
 
 
 def replay_state(g, sc, st):
@@ -271,23 +372,27 @@ def replay_state(g, sc, st):
 def run_e2e(g, sc, steps, stream, st):
     """The same steps, from the same starting state, through the C ABI with
     host buffers: each step copies the particle state in from pinned host
-    memory and the result back out."""
+    memory and the result back out.  Only converged steps earn credit."""
     import torch
     n = sc.n
     pin = lambda *shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()  # noqa: E731
     x, v, F, Cm = pin(n, 3), pin(n, 3), pin(n, 9), pin(n, 9)
     x[:], v[:], F[:], Cm[:] = st["x"], st["v"], st["F"].reshape(n, 9), st["C"].reshape(n, 9)
     stream.synchronize()
+    stats = []
     t0 = time.perf_counter()
     for _ in range(steps):
         g.set_state(x, v, F, Cm)
-        g.step(check=False)
+        stats.append(g.step(check=False))
         g.lib.mpm_get_state(g.h, x.ctypes.data, v.ctypes.data, F.ctypes.data, Cm.ctypes.data, 0)
     stream.synchronize()
     secs = time.perf_counter() - t0
     per = 8 * n * (3 + 3 + 9 + 9)
-    return {"value": n * steps / secs, "unit": UNIT, "h2d_bytes_per_step": per, "d2h_bytes_per_step": per,
-            "ms_per_step": 1e3 * secs / steps}
+    rec = step_record(stats)
+    return {"value": credited_rate(n, stats, 1e3 * secs), "unit": UNIT, "h2d_bytes_per_step": per,
+            "d2h_bytes_per_step": per, "ms_per_step": 1e3 * secs / steps,
+            "converged_steps": rec["converged"], "steps": steps, "iters": rec["iters"],
+            "status": rec["status"]}
 
 
 def run_batching(seed, steps, count=64):
@@ -328,19 +433,21 @@ def run_batching(seed, steps, count=64):
                       "half von Mises (yield 1e4 Pa), FP32 preconditioner, 3 levels, CN eps 1e-7, CFL dt"}
 
 
-def run_solvers(seed, steps=2, warmup=1):
+def run_solvers(seed, steps=4, warmup=2):
     """HOT against the paper's comparison solvers (Alg. 1: PN-PCG, PN-MGPCG)
     on the two-bar scene at dx = 1/128 (75,200 particles, FP64, CN eps 1e-7,
-    4 levels): wall time per step on the device, same steps from the same
-    state for each solver."""
+    4 levels): device time per step, the same steps from the same state for
+    each solver.  HOT runs both as printed in Alg. 3 (hierarchy built once
+    per step) and with the hierarchy refreshed every REFRESH iterations."""
     import torch
     from paper_1911_07913_gb300 import hot
-    sc = scenes.two_bars_scene(seed=seed, res=128, width=10, length=47, gap=4)
+    sc = scenes.two_bars_scene(seed=seed, res=128, width=10, length=47, gap=10)
     out = {"workload": f"two bars at dx=1/128, {sc.n} particles, FP64, CN eps 1e-7, 4 levels, {steps} steps "
                        f"after {warmup} warm-up step(s)"}
-    names = {0: "hot", 1: "pn_pcg", 2: "pn_mgpcg"}
-    for solver in (0, 1, 2):
-        opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=4, precision=0, max_iters=500, solver=solver)
+    runs = [("hot", 0, REFRESH), ("hot_alg3", 0, 0), ("pn_pcg", 1, 0), ("pn_mgpcg", 2, 0)]
+    for name, solver, refresh in runs:
+        opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=4, precision=0, max_iters=500, solver=solver,
+                                    refresh_every=refresh)
         stream = torch.cuda.Stream()
         g = hot.HotScene(sc, opts, stream=stream.cuda_stream)
         for _ in range(warmup):
@@ -348,15 +455,16 @@ def run_solvers(seed, steps=2, warmup=1):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         torch.cuda.synchronize()
         ev[0].record(stream)
-        its, inner = [], []
+        stats, inner = [], []
         for _ in range(steps):
-            st = g.step(check=False)
-            its.append(st["iters"])
+            stats.append(g.step(check=False))
             inner.append(int(sum(g.inner_iters())) if solver else 0)
         ev[1].record(stream)
         torch.cuda.synchronize()
         ms = ev[0].elapsed_time(ev[1]) / steps
-        out[names[solver]] = {"ms_per_step": ms, "outer_iters": its, "cg_iters": inner if solver else None}
+        rec = step_record(stats)
+        out[name] = {"ms_per_step": ms, "outer_iters": rec["iters"], "converged_steps": rec["converged"],
+                     "cg_iters": inner if solver else None}
         g.close()
     out["hot_speedup_vs_pn_pcg"] = out["pn_pcg"]["ms_per_step"] / out["hot"]["ms_per_step"]
     out["hot_speedup_vs_pn_mgpcg"] = out["pn_mgpcg"]["ms_per_step"] / out["hot"]["ms_per_step"]
@@ -431,65 +539,142 @@ def run_serving(seed, count=256, requests=512, workers=12, budget_gb=150.0, load
                       "every third von Mises, FP32 preconditioner, 3 levels, CN eps 1e-7; Poisson arrivals"}
 
 
-def cpu_baseline_sample():
-    """The oracle, as it stands, on a bounded sample of the same workload: the
-    two-bar scene at the same dx, materials and boundary conditions, with bars
-    of 12 x 12 x 8 cells (18,432 particles), one implicit step."""
+# --------------------------------------------------------------------------- host oracle
+# Bounded sample of the two-bar workload for the FP64 oracle: the same dx,
+# materials, hold regions and solver settings, with 6 x 6 x 12-cell bars (6,912
+# particles); the end rotation is scaled by the ratio of the free lengths
+# (7 / 85 cells) so that the twist per unit length, and hence the shear rate,
+# equals that of the 601,600-particle scene.
+SAMPLE = dict(res=256, width=6, length=12, end_cells=2, gap=8, omega=7.0 / 85.0)
+
+
+def sample_scene(seed: int = 0):
+    return scenes.two_bars_scene(seed=seed, **SAMPLE)
+
+
+def _oracle_sample_step(seed: int):
+    """One oracle step of a seeded sample (runs in a spawned worker process)."""
     from oracle import hot_oracle as O
-    sc = scenes.two_bars_scene(res=256, width=12, length=8, end_cells=2)
-    opts = workload_opts(0)
+    sc = sample_scene(seed)
     t0 = time.perf_counter()
-    out, info = O.hot_step(sc, opts)
-    secs = time.perf_counter() - t0
-    return {"value": sc.n / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one step of the two-bar scene with 12x12x8-cell bars ({sc.n} particles, "
-                      f"dx=1/256, 5 levels, CN eps=1e-7, {info['trace'].iters} L-BFGS iterations), "
-                      f"numpy/scipy FP64, single thread, {secs:.1f} s"}
+    _out, info = O.hot_step(sc, workload_opts(0))
+    return sc.n, time.perf_counter() - t0, info["trace"].iters, info["trace"].status
+
+
+def _noop(_x):
+    return 0
+
+
+def cpu_baseline_sample():
+    """The oracle, as it stands, on bounded samples of the same workload: one
+    step of the seed-0 sample on one core, then one step of an independent
+    seeded sample per host core in as many spawned processes at once (each
+    single-threaded, no shared state), timed by the wall clock."""
+    import multiprocessing as mp
+    n, secs, iters, status = _oracle_sample_step(0)
+    single = n / secs
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_noop, range(cores))              # workers up and imports done before the clock
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_sample_step, range(1, cores + 1))
+        wall = time.perf_counter() - t0
+    allcore = sum(r[0] for r in res) / wall
+    conv = sum(1 for r in res if r[3] == "ok")
+    return {"value": allcore, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one step of the two-bar sample (6x6x12-cell bars, {n} particles, dx=1/256, end rotation "
+                       f"scaled to the same twist per length, 5 levels, CN eps=1e-7, refresh every {REFRESH}), "
+                       f"numpy/scipy FP64: one process per core on {cores} independently seeded samples "
+                       f"({conv}/{cores} converged), wall {wall:.1f} s"),
+            "single_core": {"value": single, "unit": UNIT, "cores": 1, "seconds": secs, "lbfgs_iters": iters,
+                            "status": status},
+            "nproc": cores}
 
 
 def run_reference(args):
+    """The oracle arm: W + K consecutive oracle steps of the seed-0 sample on
+    the host (rank 0 only), the same metric and credit rule as the GPU arm."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     from oracle import hot_oracle as O
-    sc = scenes.two_bars_scene(res=256, width=8, length=8, end_cells=2)
+    sc = sample_scene(0)
     opts = workload_opts(0)
     state = sc
     for _ in range(args.warmup):
         state, _info = O.hot_step(state, opts)
     t0 = time.perf_counter()
-    iters = []
+    iters, status = [], []
     for _ in range(args.steps):
         state, info = O.hot_step(state, opts)
         iters.append(info["trace"].iters)
+        status.append(info["trace"].status)
     secs = time.perf_counter() - t0
-    value = sc.n * args.steps / secs
-    sample = (f"two-bar scene with 8x8x8-cell bars ({sc.n} particles, dx=1/256, 5 levels, CN eps=1e-7), "
-              f"{args.steps} consecutive steps, L-BFGS iterations {iters}")
+    conv = sum(1 for x in status if x == "ok")
+    value = sc.n * conv / secs
+    sample = (f"two-bar sample, 6x6x12-cell bars ({sc.n} particles, dx=1/256, end rotation scaled to the same twist "
+              f"per length, 5 levels, CN eps=1e-7, refresh every {REFRESH}), {args.steps} consecutive steps after "
+              f"{args.warmup} warm-up steps, {conv}/{args.steps} converged, L-BFGS iterations {iters}, one core")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": workload_desc(scenes.two_bars_scene(), workload_opts(0),
-                                    {"reference_sample": sample}),
+            "config": workload_desc(scenes.two_bars_scene(), workload_opts(0), {"reference_sample": sample}),
+            "converged_steps": conv,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
+def summarize_pair(r, sc, peaks, traffic_key_mixed, ws=1):
+    """FP64 against mixed precision on one scene from the same start state:
+    throughput (converged steps only), per-step status, and the mixed step's
+    error against the FP64 step from the same state."""
+    def arm(stats, step_ms, total_ms):
+        rec = step_record(stats, step_ms)
+        sm = sorted(step_ms)
+        return {"value": credited_rate(sc.n, stats, total_ms, ws), "unit": UNIT, "ms_per_step": total_ms / len(stats),
+                "p50_ms": float(np.percentile(sm, 50)), "p99_ms": float(np.percentile(sm, 99)),
+                "converged_steps": rec["converged"], "steps": rec["steps"], "per_step": rec}
+    p = r["partner"]
+    out = {"workload": sc.name, "particles": sc.n, "start": "the same state (after the FP64 warm-up steps)",
+           "fp64": arm(r["stats"], r["step_ms"], r["total_ms"]),
+           "mixed": arm(p["stats"], p["step_ms"], p["total_ms"])}
+    f, m = out["fp64"]["value"], out["mixed"]["value"]
+    out["speedup_mixed_over_fp64"] = (m / f) if f > 0 else None
+    errs = p.get("errors") or []
+    keys = ("grid_v_rel", "x_rel", "x_cells", "x_rel_to_step_displacement")
+    out["error_vs_fp64"] = {
+        "how": "each step k: the mixed scene steps from the FP64 state S_k; its grid v^{n+1} and particle x are "
+               "compared with the FP64 step from S_k",
+        "max": {k: max((e[k] for e in errs if e.get(k) is not None), default=None) for k in keys},
+        "per_step": [{k: (float("%.3g" % e[k]) if e.get(k) is not None else None) for k in keys} for e in errs],
+        "mixed_status_in_comparison": [int(s["status"]) for s in p.get("prof_stats", [])],
+        "mixed_iters_in_comparison": [int(s["iters"]) for s in p.get("prof_stats", [])],
+        "fp64_iters_in_comparison": [int(s["iters"]) for s in r.get("prof_stats", [])]}
+    out["roofline_mixed_vcycle"] = roofline_entry("vcycle", p.get("prof", {}), p.get("prof_stats", []), sc.n, 1,
+                                                  peaks, traffic_key=traffic_key_mixed)
+    out["mixed_kernel_ms_one_step"] = {k: round(v["ms"], 3) for k, v in p.get("breakdown", {}).items()}
+    out["mixed_clocks"] = p.get("clocks")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dominant", default="vcycle", help="kernel timed live for the roofline entry")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision arms")
+    ap.add_argument("--no-2m", action="store_true", help="skip the 2M-particle FP64 / mixed pair")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="8k-particle cube (for profiling runs)")
     ap.add_argument("--workload", default="two_bars_600k", choices=["two_bars_600k", "two_bars_2m", "cube8k"])
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--refresh", type=int, default=REFRESH, help="hierarchy refresh interval (0: Alg. 3 as printed)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-solvers", action="store_true", help="skip the HOT / PN-PCG / PN-MGPCG comparison")
@@ -497,12 +682,13 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--profile-run", action="store_true",
                     help="profiling run under ncu: warm-up and timed steps of one workload only (no breakdown, "
-                         "no roofline replay), warm-up allowed below 3")
+                         "no replay), warm-up allowed below 3")
     args = ap.parse_args()
     if args.small:
         args.workload = "cube8k"
     if args.profile_run:
-        args.no_mixed = args.no_e2e = args.no_cpu = args.no_batch = args.no_serve = args.no_solvers = True
+        args.no_mixed = args.no_2m = args.no_e2e = args.no_cpu = args.no_batch = args.no_serve = True
+        args.no_solvers = True
     elif args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -513,38 +699,42 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1911_07913_gb300 import hot
+    torch.cuda.set_device(local)
     if args.workload == "cube8k":
         sc = scenes.cube_scene(seed=rank)
         opts = scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=2e-3, levels=3, precision=args.precision)
     elif args.workload == "two_bars_2m":
         sc = scenes.two_bars_2m_scene(seed=rank)
-        opts = workload_opts(args.precision)
+        opts = workload_opts(args.precision, args.refresh)
     else:
         sc = scenes.two_bars_scene(seed=rank)
-        opts = workload_opts(args.precision)
+        opts = workload_opts(args.precision, args.refresh)
     peaks = load_peaks()
+    probe = None if args.profile_run else hot.probe_fp64_tflops()
+    partner = None
+    if not args.no_mixed and args.workload != "cube8k":
+        partner = workload_opts(1 - args.precision, args.refresh)
     barrier(ws)
-    r = run_gpu(sc, opts, args.steps, args.warmup, args.dominant, not args.no_e2e, rank, local,
-                sample_clocks=not args.profile_run, profile_run=args.profile_run)
+    r = run_gpu(sc, opts, args.steps, args.warmup, args.dominant, not args.no_e2e, local,
+                sample_clocks=not args.profile_run, profile_run=args.profile_run, partner_opts=partner,
+                fp64_probe=probe)
     barrier(ws)
     t_max = max_over_ranks(r["total_ms"], ws)
-    value = job_throughput(sc.n, ws, args.steps, t_max)
+    value = credited_rate(sc.n, r["stats"], t_max, ws)
+    prec_key = "fp64" if opts.precision == 0 else "mixed"
     roof = roofline_entry(args.dominant, r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
-                          traffic_key=f"{args.workload}_{'fp64' if opts.precision == 0 else 'mixed'}_bytes_per_vcycle")
-    mixed = None
-    if not args.no_mixed and args.workload == "two_bars_600k" and args.precision == 0:
+                          traffic_key=f"{args.workload}_{prec_key}_bytes_per_vcycle", fp64_probe=probe)
+    mixed = {}
+    if partner is not None and "partner" in r and opts.precision == 0:
+        mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_bytes_per_vcycle", ws)
+    if partner is not None and not args.no_2m and args.workload == "two_bars_600k" and opts.precision == 0:
         sc2 = scenes.two_bars_2m_scene(seed=rank)
-        o2 = workload_opts(1)
-        r2 = run_gpu(sc2, o2, args.steps, args.warmup, "vcycle", False, rank, local)
-        t2 = max_over_ranks(r2["total_ms"], ws)
-        sm = sorted(r2["step_ms"])
-        mixed = {"value": sc2.n * ws * args.steps / (t2 / 1e3), "unit": UNIT, "ms_per_step": t2 / args.steps,
-                 "p50_ms": float(np.percentile(sm, 50)), "p99_ms": float(np.percentile(sm, 99)),
-                 "config": workload_desc(sc2, o2), "iters": [s["iters"] for s in r2["stats"]],
-                 "roofline": roofline_entry("vcycle", r2["prof"], r2["prof_stats"], sc2.n, 1, peaks,
-                                            traffic_key="two_bars_2m_mixed_bytes_per_vcycle"),
-                 "kernel_ms": {k: round(v["ms"], 3) for k, v in r2["breakdown"].items()},
-                 "clocks": r2["clocks"]}
+        r2 = run_gpu(sc2, workload_opts(0, args.refresh), args.steps, args.warmup, "vcycle", False, local,
+                     partner_opts=workload_opts(1, args.refresh), fp64_probe=probe)
+        mixed["two_bars_2m"] = summarize_pair(r2, sc2, peaks, "two_bars_2m_mixed_bytes_per_vcycle", ws)
+        mixed["two_bars_2m"]["roofline_fp64_vcycle"] = roofline_entry(
+            "vcycle", r2["prof"], r2["prof_stats"], sc2.n, 0, peaks, fp64_probe=probe)
     batching = serving = solvers = None
     if args.workload == "two_bars_600k" and args.precision == 0:
         if not args.no_solvers:
@@ -558,19 +748,27 @@ def main():
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline_sample()
+    rec = step_record(r["stats"], r["step_ms"])
     sm = sorted(r["step_ms"])
+    e2e = r["e2e"]
+    if e2e is not None:
+        e2e["device_pass_iters"] = rec["iters"]
+        e2e["same_iterations_as_device_pass"] = e2e["iters"] == rec["iters"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if opts.precision == 0 else "f64+f32",
             "data": "synthetic",
-            "config": workload_desc(sc, opts, {"parallelism": f"replicas x{ws}"}),
+            "config": workload_desc(sc, opts, {"parallelism": f"replicas x{ws}",
+                                               "credit": "particle-steps of steps whose solve met the tolerance, "
+                                                         "over the time of all timed steps"}),
+            "at_tolerance": rec["converged"] == args.steps, "converged_steps": rec["converged"],
+            "per_step": rec, "warmup_status": [int(s["status"]) for s in r["warm"]],
             "p50_ms": float(np.percentile(sm, 50)), "p99_ms": float(np.percentile(sm, 99)),
-            "iters": [s["iters"] for s in r["stats"]],
-            "e2e": r["e2e"], "gpu_launches": int(r["launches"]), "roofline": roof,
+            "e2e": e2e, "gpu_launches": int(r["launches"]), "roofline": roof,
             "lbfgs_loop_on_device": r["device_loop"],
             "kernel_ms_one_step": {k: round(v["ms"], 3) for k, v in r["breakdown"].items()},
-            "clocks": r["clocks"], "mixed": mixed, "batching": batching, "serving": serving, "solvers": solvers,
-            "cpu_baseline": cpu}
+            "clocks": r["clocks"], "fp64_probe_tflops": probe, "mixed": mixed or None,
+            "batching": batching, "serving": serving, "solvers": solvers, "cpu_baseline": cpu}
     print(json.dumps(line))
 
 

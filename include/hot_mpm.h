@@ -71,14 +71,19 @@ typedef struct {
 
 /* Dirichlet box (Sec. 4.1: boundary conditions by projection).  A node whose
  * position lies in [lo, hi] (inclusive, per axis) is held: type 0 prescribes
- * v = 0, type 1 prescribes v = omega * axis x (x_i - center).  Boxes apply in
- * list order.  Independently of the list, nodes within 3 cells of the grid
- * walls are held at v = 0. */
+ * v = 0, type 1 prescribes v = omega * axis x (x_i - center).  With
+ * radius > 0 the region is the box intersected with the cylinder of that
+ * radius about the line through center along axis (axis a unit vector): a
+ * region the prescribed rotation maps onto itself, so material that starts
+ * inside stays inside as it turns.  Boxes apply in list order.
+ * Independently of the list, nodes within 3 cells of the grid walls are
+ * held at v = 0. */
 typedef struct {
   int32_t type;
   int32_t reserved;
   double lo[3], hi[3], axis[3], center[3];
   double omega;
+  double radius;
 } mpm_bc;
 
 typedef struct {
@@ -140,8 +145,8 @@ typedef struct {
   int32_t refresh_every; /* HOT only; an extension, 0 = Alg. 3 as printed (the hierarchy is
                             built once per step): every refresh_every iterations without
                             convergence, rebuild the projected Hessian and its hierarchy at
-                            the current iterate and restart the L-BFGS history.  Runs the
-                            host-driven loop. */
+                            the current iterate and restart the L-BFGS history (in the
+                            device-driven loop too, as a conditional graph node). */
   int32_t fallback_after; /* HOT only; an extension, 0 = off: a step that has not converged
                              after fallback_after L-BFGS iterations continues as PN-MGPCG
                              (Alg. 1) from the current iterate, within the same max_iters.
@@ -315,6 +320,14 @@ mpm_status mpm_server_poll(mpm_server_t server, int32_t wait, int64_t *request_i
 mpm_status mpm_server_info(mpm_server_t server, int64_t *queued, int64_t *in_flight, int64_t *in_flight_bytes,
                            int64_t *peak_in_flight_bytes);
 mpm_status mpm_server_destroy(mpm_server_t server);
+
+/* FP64 FMA throughput of the current device in TFLOP/s (2 flop per FMA),
+ * measured by timing a kernel of independent FMA chains on cuda_stream
+ * (NULL = legacy default stream); the best of three timed launches.  The
+ * paper has no counterpart: it is the denominator of the FP64-bound kernels'
+ * roofline.  Allocates one small scratch buffer.  Errors: INVALID_ARG, OOM,
+ * CUDA. */
+mpm_status mpm_probe_fp64_fma(void *cuda_stream, double *tflops);
 
 /* Elastic energy sum_p V_p psi(F_p) of a particle set, computed without any
  * device allocation.  The paper has no counterpart: this serves callers that

@@ -289,7 +289,9 @@ def boundary_conditions(sc, coords, pos):
     """Dirichlet nodes and their prescribed velocities (READING: nodes within
     three cells of the domain walls are held; boxes are applied in list
     order, a later box overriding an earlier one; a rotating box prescribes
-    omega * axis x (x_i - center))."""
+    omega * axis x (x_i - center); a box with radius > 0 holds only its
+    nodes within that distance of the rotation axis, a region that the
+    rotation it prescribes maps onto itself)."""
     n = coords.shape[0]
     fixed = np.zeros(n, bool)
     vfix = np.zeros((n, 3))
@@ -300,6 +302,16 @@ def boundary_conditions(sc, coords, pos):
         lo = np.asarray(bc.lo)
         hi = np.asarray(bc.hi)
         inside = np.all((pos >= lo) & (pos <= hi), axis=1)
+        R = getattr(bc, "radius", 0.0)
+        if R > 0.0:
+            # box intersected with the cylinder of radius R about the line
+            # through center along axis (each operation rounded separately)
+            a = np.asarray(bc.axis, np.float64)
+            r = pos - np.asarray(bc.center, np.float64)[None, :]
+            t = r[:, 0] * a[0] + r[:, 1] * a[1] + r[:, 2] * a[2]
+            q = r - t[:, None] * a[None, :]
+            d2 = q[:, 0] * q[:, 0] + q[:, 1] * q[:, 1] + q[:, 2] * q[:, 2]
+            inside &= d2 <= R * R
         fixed |= inside
         if bc.type == 0:
             vfix[inside] = 0.0
@@ -660,6 +672,25 @@ def line_search(prob: Problem, dv, p, E0, max_ls, forced_alpha=None):
     return None, E0, max_ls
 
 
+def two_loop(hist, q, apply_h0):
+    """Alg. 3's two-loop recursion: returns H q, where H is the L-BFGS inverse
+    Hessian built from the initial inverse H_0 (``apply_h0``, the V-cycle in
+    HOT) by the BFGS inverse updates of the stored pairs (s, y, rho = 1/y^T s),
+    oldest first.  First loop from the newest pair back: a_j = rho_j s_j^T q,
+    q <- q - a_j y_j; then r = H_0 q; second loop from the oldest pair on:
+    b_j = rho_j y_j^T r, r <- r + (a_j - b_j) s_j."""
+    alph = []
+    for (s, y, rho) in reversed(hist):
+        a = rho * float(np.sum(s * q))
+        q = q - a * y
+        alph.append(a)
+    r = apply_h0(q)
+    for (s, y, rho), a in zip(hist, reversed(alph)):
+        beta = rho * float(np.sum(y * r))
+        r = r + (a - beta) * s
+    return r
+
+
 def hot_solve(prob: Problem, opts, replay: Optional[Trace] = None, levels=None):
     """Alg. 3.  Returns (dv, trace).  With ``replay`` the decisions recorded
     by another implementation (iteration count, step lengths, coarse CG
@@ -725,17 +756,7 @@ def hot_solve(prob: Problem, opts, replay: Optional[Trace] = None, levels=None):
             vc_new.forced = vc.forced
             vc = vc_new
             hist = []
-        q = -g
-        alph = []
-        for (s, y, rho) in reversed(hist):
-            a = rho * float(np.sum(s * q))
-            q = q - a * y
-            alph.append(a)
-        r = vc(q)
-        for (s, y, rho), a in zip(hist, reversed(alph)):
-            beta = rho * float(np.sum(y * r))
-            r = r + (a - beta) * s
-        p = r
+        p = two_loop(hist, -g, vc)
         fb = 0
         if replay is not None:
             fb = replay.fallback[it]

@@ -100,6 +100,15 @@ __global__ void k_ls_after(LoopState *st, int max_ls, double *tr_alpha, int *tr_
   cudaGraphSetConditional(h, st->ok);
 }
 
+// hierarchy refresh (an extension of Alg. 3): every `every` iterations the
+// projected Hessian and its hierarchy are rebuilt at the current iterate and
+// the history restarts, as in the host-driven loop
+__global__ void k_refresh_decide(LoopState *st, int every, cudaGraphConditionalHandle h) {
+  const int go = st->it > 0 && st->it % every == 0;
+  if (go) st->hist_n = 0;
+  cudaGraphSetConditional(h, go);
+}
+
 __global__ void k_norms(const double *part, int nb, LoopState *st) {
   st->n0 = seq_sum(part, nb, 2, 0);
   st->n1 = seq_sum(part, nb, 2, 1);
@@ -133,7 +142,7 @@ void vc_emit(Scene &s, const double *b, double *u) {
 
 // kernels captured into each part of the graph, to count the ones it runs
 struct Counts {
-  long long top = 0, body = 0, fb1 = 0, fb2 = 0, ls = 0, upd = 0;
+  long long top = 0, body = 0, fb1 = 0, fb2 = 0, ls = 0, upd = 0, refresh = 0;
 };
 
 }  // namespace
@@ -141,8 +150,9 @@ struct Counts {
 bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double &E, double &nrm, int &it,
                       int &trials_total, mpm_status &status) {
   if (!s.loop_graph_ok || !s.graphs_ok || s.prof || (s.opts.flags & 17) || s.nn() == 0 ||
-      s.opts.refresh_every > 0 || s.opts.fallback_after > 0)
+      s.opts.fallback_after > 0)
     return false;
+  const int refresh = s.opts.refresh_every;
   // building the graph costs about as much host time as a handful of host-
   // driven iterations: by default it is used once the scene's previous solve
   // took at least DEVICE_LOOP_MIN_ITERS iterations (bit 5 forces it)
@@ -184,6 +194,15 @@ bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double 
     // one iteration of Alg. 3
     const long long b0 = launch_count();
     HOT_CUDA(cudaStreamBeginCaptureToGraph(s.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (refresh > 0) {
+      const cudaGraphConditionalHandle h_rf = new_handle(s.st);
+      k_refresh_decide<<<1, 1, 0, s.st>>>(st, refresh, h_rf);
+      HOT_LAUNCH("k_refresh_decide");
+      cudaGraph_t rf = add_conditional(s.st, h_rf, cudaGraphCondTypeIf);
+      const long long r0 = launch_count();
+      capture_into(s, 0, rf, [&] { pn_rebuild_values(s); });
+      c.refresh = launch_count() - r0;
+    }
     scale_copy(s, s.q.p, -1.0, s.g.p, n3);
     two_loop_first_dev(s, s.q.p, n3, st);
     vc_emit(s, s.q.p, s.pdir.p);
@@ -251,7 +270,7 @@ bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double 
       cudaGraph_t g = nullptr;
       HOT_CUDA(cudaStreamEndCapture(s.st, &g));
     }
-    c.body = launch_count() - b0 - c.fb1 - c.fb2 - c.ls - c.upd;
+    c.body = launch_count() - b0 - c.fb1 - c.fb2 - c.ls - c.upd - c.refresh;
     HOT_CUDA(cudaGraphInstantiate(&exec, top, 0));
   } catch (const Error &) {
     end_any_capture(s.aux_st[1]);
@@ -300,8 +319,9 @@ bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double 
     n_fb2 += f == 2;
   }
   s.graph_launches = (int)(runs + n_fb1);   // V-cycles run inside the graph
+  const long long n_refresh = (refresh > 0 && runs > 1) ? (runs - 1) / refresh : 0;
   note_launches(c.top + runs * c.body + n_fb1 * c.fb1 + n_fb2 * c.fb2 + (long long)trials_total * c.ls +
-                (long long)it * c.upd);
+                (long long)it * c.upd + n_refresh * c.refresh);
   return true;
 }
 

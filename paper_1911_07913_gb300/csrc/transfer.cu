@@ -324,6 +324,16 @@ __global__ void k_grid_finalize(int64_t n, const int *__restrict__ coords, GeoAr
     bool in = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) in = in && pos[k] >= bc.lo[k] && pos[k] <= bc.hi[k];
+    if (in && bc.radius > 0.0) {
+      // distance from the rotation axis, each operation rounded separately
+      double r0 = __dadd_rn(pos[0], -bc.center[0]), r1 = __dadd_rn(pos[1], -bc.center[1]);
+      double r2 = __dadd_rn(pos[2], -bc.center[2]);
+      double t = __dadd_rn(__dadd_rn(__dmul_rn(r0, bc.axis[0]), __dmul_rn(r1, bc.axis[1])), __dmul_rn(r2, bc.axis[2]));
+      double q0 = __dadd_rn(r0, -__dmul_rn(t, bc.axis[0])), q1 = __dadd_rn(r1, -__dmul_rn(t, bc.axis[1]));
+      double q2 = __dadd_rn(r2, -__dmul_rn(t, bc.axis[2]));
+      double d2 = __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2));
+      in = d2 <= __dmul_rn(bc.radius, bc.radius);
+    }
     if (!in) continue;
     fx = true;
     if (bc.type == 0) {

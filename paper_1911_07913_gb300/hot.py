@@ -30,7 +30,8 @@ EXPORTED = ["mpm_set_allocator", "mpm_create_scene", "mpm_destroy_scene", "mpm_l
             "mpm_batch_autotune",
             "mpm_scene_footprint", "mpm_step_batch", "mpm_profile", "mpm_profile_read",
             "mpm_kernel_launch_count", "mpm_particle_energy_noalloc", "mpm_server_create",
-            "mpm_server_submit", "mpm_server_poll", "mpm_server_info", "mpm_server_destroy"]
+            "mpm_server_submit", "mpm_server_poll", "mpm_server_info", "mpm_server_destroy",
+            "mpm_probe_fp64_fma"]
 
 
 class mpm_material(C.Structure):
@@ -41,7 +42,7 @@ class mpm_material(C.Structure):
 class mpm_bc(C.Structure):
     _fields_ = [("type", C.c_int32), ("reserved", C.c_int32), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("axis", C.c_double * 3), ("center", C.c_double * 3),
-                ("omega", C.c_double)]
+                ("omega", C.c_double), ("radius", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -220,7 +221,8 @@ class HotScene:
         bcs = (mpm_bc * max(1, len(sc.bcs)))()
         for k, b in enumerate(sc.bcs):
             bcs[k] = mpm_bc(b.type, 0, (C.c_double * 3)(*b.lo), (C.c_double * 3)(*b.hi),
-                            (C.c_double * 3)(*b.axis), (C.c_double * 3)(*b.center), b.omega)
+                            (C.c_double * 3)(*b.axis), (C.c_double * 3)(*b.center), b.omega,
+                            getattr(b, "radius", 0.0))
         if stream is None:
             try:
                 import torch
@@ -471,6 +473,16 @@ class StepServer:
             self.close()
         except Exception:
             pass
+
+
+def probe_fp64_tflops(stream: int = 0) -> float:
+    """Measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    lib = load()
+    t = C.c_double()
+    code = lib.mpm_probe_fp64_fma(C.c_void_p(stream) if stream else None, C.byref(t))
+    if code != OK:
+        raise HotError(code, lib.mpm_last_error(None).decode())
+    return t.value
 
 
 def kernel_launch_count() -> int:

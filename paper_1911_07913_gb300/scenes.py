@@ -43,6 +43,7 @@ class BoundaryBox:
     axis: tuple = (0.0, 0.0, 1.0)
     center: tuple = (0.0, 0.0, 0.0)
     omega: float = 0.0
+    radius: float = 0.0   # > 0: only nodes within this distance of the axis line through center
 
 
 @dataclasses.dataclass
@@ -162,9 +163,9 @@ def cube_scene(seed: int = 0, res: int = 32, cube_lo=(11, 4, 11), side: int = 10
 
 
 def two_bars_scene(seed: int = 0, res: int = 256, width: int = 20, length: int = 94,
-                   gap: int = 8, E_a: float = 1e5, E_b: float = 1e9, nu: float = 0.4,
+                   gap: int = 14, E_a: float = 1e5, E_b: float = 1e9, nu: float = 0.4,
                    rho: float = 2000.0, model: int = MODEL_NH, omega: float = 1.0,
-                   end_cells: int = 4, gravity=(0.0, -9.8, 0.0)) -> Scene:
+                   end_cells: int = 4, gravity=(0.0, -9.8, 0.0), hold: str = "cylinder") -> Scene:
     """Two parallel bars along z, twisted by prescribed end rotations.
 
     Stand-in for the paper's Twist scene (Fig. 1, Table 2: rho = 2000,
@@ -173,6 +174,12 @@ def two_bars_scene(seed: int = 0, res: int = 256, width: int = 20, length: int =
     E = 1e5, bar B E = 1e9, Neo-Hookean.  The ``end_cells`` end layers of
     each bar rotate about the bar axis at +omega (low-z end) and -omega
     (high-z end).
+
+    hold = "cylinder": the held region of each end is a cylinder about the
+    bar axis, 2 cells wider than the bar's half diagonal (capped half a cell
+    short of the other bar's nearest stencil node), so the turning end stays
+    inside it.  hold = "box": an axis-aligned box 3 cells wider than the bar,
+    which the end's corners leave after about 0.4 rad of rotation.
     """
     rng = np.random.default_rng(seed)
     dx = 1.0 / res
@@ -190,14 +197,22 @@ def two_bars_scene(seed: int = 0, res: int = 256, width: int = 20, length: int =
         parts.append(xb)
         mids.append(np.full(xb.shape[0], b, np.int32))
         center = (0.5 * (x0 + x1) * dx, 0.5 * (y0 + y1) * dx, 0.0)
-        lo_x, hi_x = (x0 - 3) * dx, (x1 + 3) * dx
-        lo_y, hi_y = (y0 - 3) * dx, (y1 + 3) * dx
+        if hold == "cylinder":
+            reach = gap + 0.5 * width - 1.0          # axis -> other bar's nearest stencil node, cells
+            radius = min(np.sqrt(0.5) * width + 2.0, reach - 0.5)
+            lo_x, hi_x = center[0] - radius * dx, center[0] + radius * dx
+            lo_y, hi_y = center[1] - radius * dx, center[1] + radius * dx
+            rad = radius * dx
+        else:
+            lo_x, hi_x = (x0 - 3) * dx, (x1 + 3) * dx
+            lo_y, hi_y = (y0 - 3) * dx, (y1 + 3) * dx
+            rad = 0.0
         bcs.append(BoundaryBox(BC_ROTATE, (lo_x, lo_y, (z0 - 3) * dx),
                                (hi_x, hi_y, (z0 + end_cells + 0.5) * dx),
-                               (0.0, 0.0, 1.0), center, omega))
+                               (0.0, 0.0, 1.0), center, omega, rad))
         bcs.append(BoundaryBox(BC_ROTATE, (lo_x, lo_y, (z1 - end_cells - 0.5) * dx),
                                (hi_x, hi_y, (z1 + 3) * dx),
-                               (0.0, 0.0, 1.0), center, -omega))
+                               (0.0, 0.0, 1.0), center, -omega, rad))
     x = np.concatenate(parts)
     mat = np.concatenate(mids)
     v = np.zeros_like(x)
@@ -208,7 +223,7 @@ def two_bars_scene(seed: int = 0, res: int = 256, width: int = 20, length: int =
 def two_bars_2m_scene(seed: int = 0) -> Scene:
     """The two-bar scene at 1.5x resolution: dx = 1/384, bars 30 x 30 x 141
     cells, 8 particles per cell (2,030,400 particles)."""
-    return two_bars_scene(seed=seed, res=384, width=30, length=141, gap=12)
+    return two_bars_scene(seed=seed, res=384, width=30, length=141, gap=18)
 
 
 def tiny_scene(seed: int = 0, res: int = 8, cells=(2, 2, 2), lo=(3, 3, 3), ppc_axis: int = 1,

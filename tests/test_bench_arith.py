@@ -3,6 +3,7 @@ V-cycle, the achieved rate and fraction, and the whole-job throughput."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -50,3 +51,54 @@ def test_roofline_fraction_and_bound():
 def test_job_throughput_is_whole_job_over_slowest_rank():
     # 4 ranks, 1000 units each, 5 steps, slowest rank 250 ms
     assert bench.job_throughput(1000, 4, 5, 250.0) == pytest.approx(4 * 1000 * 5 / 0.25)
+
+
+def _st(status, iters=10, norm=1e-6, dt=1e-2):
+    return {"status": status, "iters": iters, "final_norm": norm, "dt": dt}
+
+
+def test_only_converged_steps_earn_particle_steps():
+    """A step that stopped at the iteration cap costs its time and earns
+    nothing: 3 of 4 steps converged over 2 s -> 3 N / 2 s."""
+    stats = [_st(0), _st(4, 500), _st(0), _st(0)]
+    assert bench.credited_rate(1000, stats, 2000.0) == pytest.approx(1500.0)
+    assert bench.credited_rate(1000, stats, 2000.0, ws=2) == pytest.approx(3000.0)
+    rec = bench.step_record(stats, [1.0, 2.0, 3.0, 4.0])
+    assert rec["converged"] == 3 and rec["steps"] == 4
+    assert rec["status"] == [0, 4, 0, 0] and rec["iters"] == [10, 500, 10, 10] and rec["ms"][3] == 4.0
+
+
+def test_mixed_error_metrics():
+    c = np.arange(12).reshape(4, 3)
+    v64 = np.ones((4, 3))
+    v32 = v64.copy()
+    v32[2, 1] += 1e-6
+    xp = np.full((2, 3), 0.5)
+    x64 = xp + 1e-3
+    x32 = x64.copy()
+    x32[1, 0] += 2e-9
+    e = bench.mixed_error(c, v64, x64, c, v32, x32, xp, 0.01)
+    assert e["grid_v_rel"] == pytest.approx(1e-6)
+    assert e["x_rel"] == pytest.approx(2e-9 / 0.501)
+    assert e["x_cells"] == pytest.approx(2e-7)
+    assert e["x_rel_to_step_displacement"] == pytest.approx(2e-6)
+    e2 = bench.mixed_error(c, v64, x64, c[::-1].copy(), v32, x32, xp, 0.01)
+    assert e2["grid_v_rel"] is None
+
+
+def test_pair_summary_speedup_and_error_maxima():
+    class Sc:
+        n, name = 100, "s"
+    stats64 = [_st(0), _st(0)]
+    stats32 = [_st(0), _st(4, 500)]
+    errs = [{"grid_v_rel": 1e-6, "x_rel": 1e-9, "x_cells": 1e-5, "x_rel_to_step_displacement": 1e-4},
+            {"grid_v_rel": 3e-6, "x_rel": 2e-9, "x_cells": 3e-5, "x_rel_to_step_displacement": 2e-4}]
+    r = {"stats": stats64, "step_ms": [10.0, 10.0], "total_ms": 20.0, "prof_stats": stats64,
+         "partner": {"stats": stats32, "step_ms": [4.0, 6.0], "total_ms": 10.0, "errors": errs,
+                     "prof_stats": stats32}}
+    out = bench.summarize_pair(r, Sc(), {"hbm_gbs": 5000.0}, None)
+    assert out["fp64"]["value"] == pytest.approx(200 / 0.02)
+    assert out["mixed"]["value"] == pytest.approx(100 / 0.01)      # one converged step of two
+    assert out["speedup_mixed_over_fp64"] == pytest.approx(1.0)
+    assert out["error_vs_fp64"]["max"]["grid_v_rel"] == pytest.approx(3e-6)
+    assert out["mixed"]["converged_steps"] == 1

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_struct_sizes_match_header(lib_path):
     # sizes follow from the C layout rules on LP64 (x86-64 and aarch64 alike)
     assert ctypes.sizeof(hot.mpm_material) == 40
-    assert ctypes.sizeof(hot.mpm_bc) == 8 + 12 * 8 + 8
+    assert ctypes.sizeof(hot.mpm_bc) == 8 + 12 * 8 + 8 + 8
     assert ctypes.sizeof(hot.mpm_solver_opts) == 8 + 8 * 4 + 3 * 8 + 8 + 8
     assert ctypes.sizeof(hot.mpm_step_stats) == 16 + 24 + 8 + 128 + 8 + 8
 

@@ -24,10 +24,13 @@ def hot():
 
 
 def make_scenes():
-    bars = scenes.two_bars_scene(seed=3, res=64, width=6, length=14, gap=4, E_a=1e5, E_b=1e8)
+    bars = scenes.two_bars_scene(seed=3, res=64, width=6, length=14, gap=4, E_a=1e5, E_b=1e8, hold="box")
+    # the benchmark's form of the scene: cylindrical hold regions about each bar axis
+    bars_cyl = scenes.two_bars_scene(seed=4, res=64, width=6, length=14, gap=8, E_a=1e5, E_b=1e8)
     return {
         "cube8k_fcr": (scenes.cube_scene(seed=0), scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=2e-3, levels=3)),
         "bars_nh_cn": (bars, scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3)),
+        "bars_cyl": (bars_cyl, scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3)),
         "cube_small_l1": (scenes.cube_scene(seed=5, res=16, cube_lo=(5, 4, 5), side=3),
                           scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=3e-3, levels=1)),
     }
@@ -180,15 +183,17 @@ def test_vcycle_launch_modes_bitwise(hot, precision):
         assert np.array_equal(u, out[0][0])
 
 
-@pytest.mark.parametrize("name", ["bars_nh_cn", "cube8k_fcr", "cube_von_mises"])
-def test_device_loop_matches_host_loop(hot, name):
+@pytest.mark.parametrize("name,refresh", [("bars_nh_cn", 0), ("cube8k_fcr", 0), ("cube_von_mises", 0),
+                                          ("bars_cyl", 0), ("bars_cyl", 3), ("bars_nh_cn", 2)])
+def test_device_loop_matches_host_loop(hot, name, refresh):
     """The L-BFGS iterations as one CUDA graph with device-side decisions take
     the same decisions as the host-driven loop and reach the same iterate
-    (P2G and gradient scatters use FP64 atomics, so sums agree to rounding)."""
+    (P2G and gradient scatters use FP64 atomics, so sums agree to rounding);
+    with the hierarchy refresh as a conditional graph node too."""
     sc, opts = SCENES[name]
     runs = {}
     for flags in (32, 16):
-        g = hot.HotScene(sc, scenes.SolverOptions(**{**opts.__dict__, "flags": flags}))
+        g = hot.HotScene(sc, scenes.SolverOptions(**{**opts.__dict__, "flags": flags, "refresh_every": refresh}))
         g.p2g()
         st = g.solve()
         runs[flags] = (st, g.trace(), g.grid()["dv"])
@@ -238,15 +243,17 @@ def test_projected_newton_replay_parity(hot, name, solver):
         assert np.sqrt(np.sum(gr * gr)) <= opts.eps * np.sqrt(np.sum(prob.gradient(0 * dv) ** 2)) * (1 + 1e-6)
 
 
-def test_refresh_extension_replay_parity(hot):
+@pytest.mark.parametrize("name,flags", [("bars_nh_cn", 0), ("bars_cyl", 0), ("bars_cyl", 32)])
+def test_refresh_extension_replay_parity(hot, name, flags):
     """Hierarchy refresh every 3 iterations (extension of Alg. 3): the oracle
-    with the same refresh replays the GPU's decisions to the same Δv."""
-    sc, opts = SCENES["bars_nh_cn"]
-    opts = scenes.SolverOptions(**{**opts.__dict__, "refresh_every": 3})
+    with the same refresh replays the GPU's decisions to the same Δv, from
+    the host-driven loop and from the device-driven graph (flag bit 5)."""
+    sc, opts = SCENES[name]
+    opts = scenes.SolverOptions(**{**opts.__dict__, "refresh_every": 3, "flags": flags})
     g = hot.HotScene(sc, opts)
     g.p2g()
     st = g.solve()
-    assert st["status"] == 0 and st["iters"] > 3 and st["device_loop"] == 0
+    assert st["status"] == 0 and st["iters"] > 3 and st["device_loop"] == (1 if flags & 32 else 0)
     tr = g.trace()
     dv = g.grid()["dv"]
     g.close()

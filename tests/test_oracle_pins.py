@@ -267,6 +267,25 @@ def test_boundary_conditions_rotation_box():
     np.testing.assert_allclose(g.v[held][:, 2], 0.0, atol=1e-15)
 
 
+def test_boundary_conditions_rotation_cylinder():
+    """A box with radius > 0 holds exactly its nodes whose distance from the
+    rotation axis (|axis x (x_i - c)|, an independent formula) is at most the
+    radius; the held velocity is the rigid rotation."""
+    sc = free_scene(3)
+    ax = np.array([0.0, 0.0, 1.0])
+    c = np.array([0.47, 0.52, 0.0])
+    bc = scenes.BoundaryBox(scenes.BC_ROTATE, (0, 0, 0), (1, 1, 0.43), tuple(ax), tuple(c), -1.5, 0.09)
+    sc.bcs = [bc]
+    g = O.p2g(sc)
+    dist = np.linalg.norm(np.cross(ax[None, :], g.pos - c[None, :]), axis=1)
+    held = (g.pos[:, 2] <= 0.43) & (dist <= 0.09)
+    assert held.any() and (~held).any()
+    assert np.array_equal(g.fixed, held)
+    r = g.pos[held] - c
+    np.testing.assert_allclose(g.v[held][:, 0], 1.5 * r[:, 1], atol=1e-15)
+    np.testing.assert_allclose(g.v[held][:, 1], -1.5 * r[:, 0], atol=1e-15)
+
+
 # ---------------------------------------------------------------- E, grad E, hess E
 @pytest.mark.parametrize("model", [0, 1])
 def test_energy_gradient_hessian_finite_difference(model):
@@ -728,3 +747,114 @@ def test_fallback_extension_finishes_with_newton_and_replays():
     assert np.all(np.diff(tr.energies) <= 0)
     dv2, _ = O.hot_solve(prob, opts, replay=tr)
     np.testing.assert_array_equal(dv2, dv)
+
+
+# ---------------------------------------------------------------- L-BFGS two-loop (Alg. 3)
+def _pairs(rng, n, m, A=None):
+    """m pairs (s, y, 1/y^T s) with positive curvature; y = A s when A is given."""
+    hist = []
+    if A is None:
+        B = rng.normal(size=(n, n))
+        A_ = B @ B.T + n * np.eye(n)
+    else:
+        A_ = A
+    for _ in range(m):
+        s = rng.normal(size=n)
+        y = A_ @ s if A is not None else A_ @ s + 0.1 * rng.normal(size=n)
+        ys = float(y @ s)
+        assert ys > 0
+        hist.append((s.reshape(-1, 3), y.reshape(-1, 3), 1.0 / ys))
+    return hist
+
+
+def _dense_bfgs_inverse(H0, hist):
+    """The inverse-Hessian BFGS update applied pair by pair, oldest first:
+    H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T."""
+    H = H0.copy()
+    n = H.shape[0]
+    for s, y, rho in hist:
+        s, y = s.ravel(), y.ravel()
+        V = np.eye(n) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    return H
+
+
+def _spd(rng, n):
+    B = rng.normal(size=(n, n))
+    return B @ B.T + 0.5 * n * np.eye(n)
+
+
+@pytest.mark.parametrize("m", [0, 1, 3, 8])
+def test_two_loop_equals_dense_bfgs_inverse_updates(m):
+    """The two-loop recursion computes H q for the matrix obtained from H_0 by
+    the m BFGS inverse updates (Nocedal & Wright, Alg. 7.4 against Eq. 6.17)."""
+    rng = np.random.default_rng(40 + m)
+    n = 24
+    H0 = _spd(rng, n)
+    hist = _pairs(rng, n, m)
+    q = rng.normal(size=(n // 3, 3))
+    got = O.two_loop(hist, q, lambda v: (H0 @ v.ravel()).reshape(v.shape))
+    want = (_dense_bfgs_inverse(H0, hist) @ q.ravel()).reshape(q.shape)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_two_loop_secant_condition_and_quadratic_invariance():
+    """The newest pair satisfies the secant equation H y = s; on a quadratic
+    with y_j = A s_j and H_0 = A^{-1}, every update keeps H = A^{-1}, so the
+    first L-BFGS direction is the Newton step."""
+    rng = np.random.default_rng(7)
+    n = 18
+    H0 = _spd(rng, n)
+    hist = _pairs(rng, n, 5)
+    h0 = lambda v: (H0 @ v.ravel()).reshape(v.shape)  # noqa: E731
+    s_new, y_new, _ = hist[-1]
+    got = O.two_loop(hist, y_new, h0)
+    assert np.abs(got - s_new).max() <= 1e-11 * np.abs(s_new).max()
+    A = _spd(rng, n)
+    Ainv = np.linalg.inv(A)
+    histA = _pairs(rng, n, 6, A=A)
+    q = rng.normal(size=(n // 3, 3))
+    got = O.two_loop(histA, q, lambda v: (Ainv @ v.ravel()).reshape(v.shape))
+    want = (Ainv @ q.ravel()).reshape(q.shape)
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_two_loop_pins_catch_planted_mistakes():
+    """Each plausible slip in the recursion -- loop order swapped, the a - beta
+    update reduced to -beta, rho taken from the neighbouring pair -- breaks
+    the dense-update pin above (planted in copies of the recursion)."""
+    def swapped(hist, q, h0):
+        alph = []
+        for (s, y, rho) in hist:                     # oldest first in the first loop
+            a = rho * float(np.sum(s * q))
+            q = q - a * y
+            alph.append(a)
+        r = h0(q)
+        for (s, y, rho), a in zip(reversed(hist), reversed(alph)):
+            r = r + (a - rho * float(np.sum(y * r))) * s
+        return r
+
+    def dropped_a(hist, q, h0):
+        for (s, y, rho) in reversed(hist):
+            q = q - rho * float(np.sum(s * q)) * y
+        r = h0(q)
+        for (s, y, rho) in hist:
+            r = r - rho * float(np.sum(y * r)) * s
+        return r
+
+    def wrong_rho(hist, q, h0):
+        rhos = [h[2] for h in hist]
+        rhos = rhos[1:] + rhos[:1]
+        h2 = [(s, y, r) for (s, y, _), r in zip(hist, rhos)]
+        return O.two_loop(h2, q, h0)
+
+    rng = np.random.default_rng(11)
+    n = 24
+    H0 = _spd(rng, n)
+    hist = _pairs(rng, n, 4)
+    q = rng.normal(size=(n // 3, 3))
+    h0 = lambda v: (H0 @ v.ravel()).reshape(v.shape)  # noqa: E731
+    want = (_dense_bfgs_inverse(H0, hist) @ q.ravel()).reshape(q.shape)
+    assert np.abs(O.two_loop(hist, q, h0) - want).max() <= 1e-12 * np.abs(want).max()
+    for bad in (swapped, dropped_a, wrong_rho):
+        assert np.abs(bad(hist, q, h0) - want).max() > 1e-6 * np.abs(want).max(), bad.__name__
