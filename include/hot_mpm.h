@@ -114,8 +114,9 @@ typedef struct {
                             coarse solve, FP64 energy/gradient/L-BFGS/CN */
   int32_t max_iters;     /* L-BFGS iteration cap */
   int32_t max_ls;        /* line-search halvings cap */
-  int32_t max_coarse_cg; /* coarsest-level PCG cap; 0 = number of coarse DOFs, at most 100 when
-                            the V-cycle runs in FP32 (precision 1) */
+  int32_t max_coarse_cg; /* coarsest-level PCG cap; 0 = number of coarse DOFs, at most 200 when
+                            the V-cycle runs in FP32 (precision 1; the coarsest PCG then computes
+                            in FP64 on the FP32 matrix) */
   int32_t record_trace;  /* 1: keep the decision trace (mpm_get_trace) */
   double dt;             /* > 0: fixed step; else min(1/fps, cfl dx / v_max) */
   double fps;
@@ -247,6 +248,17 @@ mpm_status mpm_get_hessian(mpm_scene_t s, int32_t level, int64_t *n_rows, int64_
  * coarsest PCG count (may be NULL).  Held DOFs of b are ignored, of u zero. */
 mpm_status mpm_apply_vcycle(mpm_scene_t s, const double *b, double *u, int32_t *cg_iters);
 
+/* Poll limit of the scene's device-side waits: the grid barrier between the
+ * colors of a cooperative Gauss-Seidel sweep and the cooperative coarsest
+ * PCG's barriers.  A wait that polls `polls` times without the other blocks
+ * arriving gives up: the kernel records the timeout and returns, and the call
+ * that launched it returns MPM_ERR_TIMEOUT (its numeric result is then
+ * meaningless; the scene stays usable).  Default 2^24 polls (seconds); the
+ * paper has no counterpart: this bounds every wait so that a failure cannot
+ * hang the GPU, and a small limit lets a test exercise that path.  Errors:
+ * INVALID_ARG (polls < 1). */
+mpm_status mpm_set_wait_limit(mpm_scene_t s, int64_t polls);
+
 /* Decision trace of the last solve (record_trace = 1): iteration count,
  * accepted step lengths, line-search trials, skipped L-BFGS pairs and
  * restarts per iteration, coarse PCG counts per V-cycle.  Arrays of
@@ -331,11 +343,11 @@ mpm_status mpm_probe_fp64_fma(void *cuda_stream, double *tflops);
 
 /* Elastic energy sum_p V_p psi(F_p) of a particle set, computed without any
  * device allocation.  The paper has no counterpart: this serves callers that
- * cannot allocate at the point of the call -- code running while a stream is
- * captured into a CUDA graph (cudaMalloc would break or be refused by the
- * capture), real-time loops that cannot afford the device synchronisation
- * cudaMalloc/cudaFree imply, and hosts with a fixed, pre-reserved memory
- * budget.  Every other entry point allocates through the allocator hook.
+ * cannot allocate at the point of the call -- real-time loops that cannot
+ * afford the device synchronisation cudaMalloc/cudaFree imply, hosts whose
+ * device memory is a fixed budget reserved up front by their own pool, and
+ * code paths that may not enter an allocator at all.  Every other entry
+ * point allocates through the allocator hook.
  *
  * F (n x 9 row-major), vol (n) and material_id (n, may be NULL = material 0;
  * an id outside [0, n_materials) makes the result NaN) are device pointers; materials is a host array of 1..16 entries (models 0
@@ -346,9 +358,10 @@ mpm_status mpm_probe_fp64_fma(void *cuda_stream, double *tflops);
  * Scratch: a fixed 512 KiB array in the library's device memory, held on
  * every GPU that loads the library until the process exits.  Hence the
  * limit n_particles <= 134,217,728 (2048 particles per partial sum); larger
- * sets are rejected with MPM_ERR_INVALID_ARG.  The first call on a device
- * looks the array's address up (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  All calls share
+ * sets are rejected with MPM_ERR_INVALID_ARG.  The first call in a CUDA
+ * context (per device, and again after a cudaDeviceReset) looks the array's
+ * address up (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  All calls share
  * the array: calls whose work overlaps on the GPU (different streams, or
  * other threads) race and must be serialised by the caller.  Errors:
  * INVALID_ARG, CUDA; message in mpm_last_error(NULL). */

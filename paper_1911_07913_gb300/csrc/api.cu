@@ -918,7 +918,19 @@ mpm_status mpm_apply_vcycle(mpm_scene_t sc, const double *b, double *u, int32_t 
     HOT_CUDA(cudaStreamSynchronize(s->st));
     std::vector<int> lg = read_log(*s);
     if (cg_iters) *cg_iters = lg.empty() ? 0 : lg.back();
-    if (read_errflag(*s) & DEV_ERR_TIMEOUT) fail(MPM_ERR_TIMEOUT, "coarse solve barrier timed out");
+    if (read_errflag(*s) & DEV_ERR_TIMEOUT) fail(MPM_ERR_TIMEOUT, "a device-side barrier of the V-cycle timed out");
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_set_wait_limit(mpm_scene_t sc, int64_t polls) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    if (polls < 1) fail(MPM_ERR_INVALID_ARG, "polls must be >= 1");
+    HOT_CUDA(cudaStreamSynchronize(s->st));
+    s->spin_limit = polls;
+    s->drop_graph();   // captured launches carry the old limit
     return MPM_OK;
   });
 }

@@ -162,6 +162,7 @@ struct Scene {
   bool has_grid = false;       // a P2G has run; its grid stays readable until the next one
   bool has_solution = false;   // dv holds the last solve of that grid
   double dt = 0.0;
+  long long spin_limit = 1ll << 24;   // polls before a device-side wait gives up (mpm_set_wait_limit)
 
   // particles (sorted by cell after P2G); pd: PF_COUNT fields, SoA
   DBuf<double> pd, pd_alt;

@@ -382,22 +382,24 @@ constexpr int RPW = 32 / RL;   // rows per warp
 
 // Partial sums of (H u)_i over the blocks this lane visits, as explicit FMA
 // chains (the FP64 pipe is the bound of these kernels: 9 FMA per block).
-template <class T>
+// matrix values of type T, vector and sums of type U (U = T, or double over
+// a float matrix on the coarsest level)
+template <class T, class U = T>
 __device__ __forceinline__ void row_partial(int64_t i, bool valid, int lane, const int *__restrict__ row_ptr,
                                             const int *__restrict__ cols, const T *__restrict__ vals,
-                                            const T *u, bool skip_diag, T acc[3]) {
-  acc[0] = acc[1] = acc[2] = T(0);
+                                            const U *u, bool skip_diag, U acc[3]) {
+  acc[0] = acc[1] = acc[2] = U(0);
   if (!valid) return;
   const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp;
   const T *v = vals + 9 * (int64_t)rp;
 #pragma unroll 2
   for (int b = lane; b < nb; b += RL) {
     int j = cols[rp + b];
-    T h[9];
+    U h[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) h[e] = v[e * nb + b];
+    for (int e = 0; e < 9; ++e) h[e] = (U)v[e * nb + b];
     if (skip_diag && j == i) continue;
-    const T u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
+    const U u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
     acc[0] = fma(h[0], u0, acc[0]);
     acc[1] = fma(h[3], u0, acc[1]);
     acc[2] = fma(h[6], u0, acc[2]);
@@ -491,6 +493,11 @@ __device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int r
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int q = 0; q < SW_PRE; ++q) {
+    // FP64: a warp-wide FP64 instruction holds the SM's FP64 pipe whether or
+    // not its lanes are predicated on, so chunks past the used blocks are
+    // skipped by a warp-uniform branch.  FP32: no branch, so the u gathers of
+    // every chunk issue together.
+    if (sizeof(T) == 8 && 32 * q >= nuse) break;
     const int j = R.j[q];
     if (j < 0 || j == i) continue;
     const T u0 = ld_u<T, LDCG>(u + 3 * j), u1 = ld_u<T, LDCG>(u + 3 * j + 1), u2 = ld_u<T, LDCG>(u + 3 * j + 2);
@@ -568,6 +575,7 @@ __global__ void k_residual(int64_t n, const int *__restrict__ row_ptr, const int
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int q = 0; q < SW_PRE; ++q) {
+    if (sizeof(T) == 8 && 32 * q >= nb) break;   // FP64: skip unused chunks (warp-uniform)
     if (j[q] < 0) continue;
     const T u0 = u[3 * j[q]], u1 = u[3 * j[q] + 1], u2 = u[3 * j[q] + 2];
     acc[0] = fma(h[q][0], u0, acc[0]);
@@ -676,9 +684,9 @@ __global__ void k_store_out(int64_t n, const T *__restrict__ src, const uint8_t 
 // order, so all blocks take the same branch.  The grid barrier gives up after
 // a bounded number of polls and reports DEV_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------
-constexpr long long BARRIER_SPIN_LIMIT = 1ll << 24;
-
-__device__ bool grid_sync(unsigned *bar, unsigned &gen, int *err) {
+// every spin wait gives up after the scene's poll limit (mpm_set_wait_limit;
+// default 1 << 24 polls), sets DEV_ERR_TIMEOUT and returns
+__device__ bool grid_sync(unsigned *bar, unsigned &gen, int *err, long long spin_limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -692,7 +700,7 @@ __device__ bool grid_sync(unsigned *bar, unsigned &gen, int *err) {
     } else {
       long long spins = 0;
       while (*((volatile unsigned *)&bar[1]) == gen) {
-        if (!keep_waiting(spins, BARRIER_SPIN_LIMIT)) {
+        if (!keep_waiting(spins, spin_limit)) {
           ok = 0;
           atomicOr(err, DEV_ERR_TIMEOUT);
           break;
@@ -749,7 +757,7 @@ template <class T, bool MULTI, bool CLUSTER = false>
 __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, const int4 *__restrict__ rec,
                                                              const int *__restrict__ cols, const T *__restrict__ vals,
                                                              const T *__restrict__ dinv, const T *__restrict__ b, T *u,
-                                                             unsigned *bar, int *err) {
+                                                             unsigned *bar, int *err, long long spin_limit) {
   __shared__ int4 s_rec[54][SW_WARPS];
   __shared__ int s_ok;
   const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -777,9 +785,9 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, con
       for (int g = first + G * SW_WARPS; g < plan.nr[k]; g += G * SW_WARPS) {
         const int4 r2 = rec[plan.off[k] + g];
         const int nuse2 = k < plan.low_steps ? r2.w : r2.z;
-        RowRegs<T> R2;
-        load_row<T>(R2, r2.x, r2.y, r2.z, nuse2, lane, cols, vals, dinv, b);
-        update_row<T, true>(R2, r2.x, r2.y, r2.z, nuse2, lane, cols, vals, u);
+        // the registers of the row just updated are free: reuse them
+        load_row<T>(R, r2.x, r2.y, r2.z, nuse2, lane, cols, vals, dinv, b);
+        update_row<T, true>(R, r2.x, r2.y, r2.z, nuse2, lane, cols, vals, u);
       }
     }
     if (k + 1 == plan.steps) break;
@@ -800,7 +808,7 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, con
     if (threadIdx.x == 0) {
       long long spins = 0;
       while (bar_load_acquire(bar) < target) {
-        if (!keep_waiting(spins, BARRIER_SPIN_LIMIT)) {
+        if (!keep_waiting(spins, spin_limit)) {
           s_ok = 0;
           atomicOr(err, DEV_ERR_TIMEOUT);
           break;
@@ -817,7 +825,7 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
                                                    const T *__restrict__ vals, const T *__restrict__ diag,
                                                    const T *__restrict__ b, T *x, T *r, T *z, T *p, T *Ap,
                                                    double *part, unsigned *bar, int *log, int *log_idx, int log_cap,
-                                                   int *err, double tau, int max_iter) {
+                                                   int *err, double tau, int max_iter, long long spin_limit) {
   __shared__ double sh[NT];
   unsigned gen = 0;
   const int64_t n3 = 3 * n;
@@ -837,7 +845,7 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
   }
   double t = block_sum<NT>(acc, sh);
   if (threadIdx.x == 0) partA[blockIdx.x] = t;
-  if (!grid_sync(bar, gen, err)) return;
+  if (!grid_sync(bar, gen, err, spin_limit)) return;
   double rz = sum_partials<NT>(partA, G, sh);
   const double bn = sqrt(fmax(rz, 0.0));
   // in float32 a relative residual below ~1e-3 is not reliably reachable;
@@ -864,7 +872,7 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
     }
     t = block_sum<NT>(acc, sh);
     if (threadIdx.x == 0) partB[blockIdx.x] = t;
-    if (!grid_sync(bar, gen, err)) return;
+    if (!grid_sync(bar, gen, err, spin_limit)) return;
     double pAp = sum_partials<NT>(partB, G, sh);
     if (!(pAp > 0.0)) break;
     const double alpha = rz / pAp;
@@ -880,13 +888,13 @@ __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restr
     }
     t = block_sum<NT>(acc, sh);
     if (threadIdx.x == 0) partA[blockIdx.x] = t;
-    if (!grid_sync(bar, gen, err)) return;
+    if (!grid_sync(bar, gen, err, spin_limit)) return;
     double rz_new = sum_partials<NT>(partA, G, sh);
     const double beta = rz_new / rz;
     rz = rz_new;
     for (int64_t k = gtid; k < n3; k += gstride) p[k] = z[k] + (T)beta * p[k];
     ++it;
-    if (!grid_sync(bar, gen, err)) return;
+    if (!grid_sync(bar, gen, err, spin_limit)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int k = *log_idx;
@@ -948,7 +956,7 @@ __device__ __forceinline__ double cta_sum_first(double v, int nz, double *ws) {
   return cta_sum_lane0(v, ws);
 }
 
-template <class T>
+template <class T, class V>
 __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__restrict__ row_ptr,
                                                             const int *__restrict__ gcols,
                                                             const T *__restrict__ gvals,
@@ -966,13 +974,13 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
   const int rank = (int)cluster.block_rank();
   double *redP = reinterpret_cast<double *>(sm);   // partials p^T Ap, by rank
   double *redR = redP + CLMAX;                     // partials r^T z, by rank
-  T *pfull = reinterpret_cast<T *>(redR + CLMAX);
-  T *zfull = pfull + 3 * R;
-  T *x = zfull + 3 * R;
-  T *r = x + 3 * rows_max;
-  T *Ap = r + 3 * rows_max;
-  T *dg = Ap + 3 * rows_max;
-  T *vals = dg + 3 * rows_max;
+  V *pfull = reinterpret_cast<V *>(redR + CLMAX);
+  V *zfull = pfull + 3 * R;
+  V *x = zfull + 3 * R;
+  V *r = x + 3 * rows_max;
+  V *Ap = r + 3 * rows_max;
+  V *dg = Ap + 3 * rows_max;
+  V *vals = dg + 3 * rows_max;   // converted to V once, as the level is staged
   int *rptr = reinterpret_cast<int *>(vals + 9 * (int64_t)nb_max);
   int *cols = rptr + rows_max + 1;
   const int r0 = plan.bounds[rank], r1 = plan.bounds[rank + 1], nr = r1 - r0;
@@ -983,15 +991,15 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
 #pragma unroll 4
   for (int k = threadIdx.x; k < nbl; k += CNT) cols[k] = gcols[g0 + k];
 #pragma unroll 8
-  for (int k = threadIdx.x; k < 9 * nbl; k += CNT) vals[k] = gvals[9 * (int64_t)g0 + k];
+  for (int k = threadIdx.x; k < 9 * nbl; k += CNT) vals[k] = (V)gvals[9 * (int64_t)g0 + k];
   // x = 0, r = b, z = D^-1 r (slices to every CTA), partial r^T z
   double acc = 0.0;
   for (int k = threadIdx.x; k < 3 * nr; k += CNT) {
-    const T d = gdiag[3 * r0 + k], bk = b[3 * r0 + k];
+    const V d = (V)gdiag[3 * r0 + k], bk = (V)b[3 * r0 + k];
     dg[k] = d;
-    x[k] = T(0);
+    x[k] = V(0);
     r[k] = bk;
-    const T zk = bk / d;
+    const V zk = bk / d;
     for (int dst = 0; dst < cl; ++dst) cluster.map_shared_rank(zfull, dst)[3 * r0 + k] = zk;
     acc += (double)bk * (double)zk;
   }
@@ -1003,8 +1011,8 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
   if (threadIdx.x == 0) {
     for (int k = 0; k < cl; ++k) rz += redR[k];
     bn = sqrt(fmax(rz, 0.0));
-    // in float32 a relative residual below ~1e-3 is not reliably reachable
-    kk = fmax(fmin(0.5, sqrt(fmax(bn, tau))), sizeof(T) == 4 ? 1e-3 : 0.0);
+    // in float32 arithmetic a relative residual below ~1e-3 is not reliably reachable
+    kk = fmax(fmin(0.5, sqrt(fmax(bn, tau))), sizeof(V) == 4 ? 1e-3 : 0.0);
     s_stop = (sqrt(fmax(rz, 0.0)) <= kk * bn || max_iter <= 0) ? 1 : 0;
   }
   for (int k = threadIdx.x; k < 3 * R; k += CNT) pfull[k] = zfull[k];   // p = z
@@ -1015,9 +1023,9 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
     // three components of a row after the split warp sum)
     double accw = 0.0;
     for (int i = warp; i < nr; i += CNW) {
-      T a3[3];
-      row_partial<T>(i, true, lane, rptr, cols, vals, pfull, false, a3);
-      const T sc = warp_sum3_split<T>(a3, lane);
+      V a3[3];
+      row_partial<V, V>(i, true, lane, rptr, cols, vals, pfull, false, a3);
+      const V sc = warp_sum3_split<V>(a3, lane);
       if ((lane & 7) == 0 && lane < 24) {
         const int c = lane >> 3;
         Ap[3 * i + c] = sc;
@@ -1036,13 +1044,13 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
     }
     __syncthreads();
     if (s_stop) break;
-    const T alpha = (T)s_alpha;
+    const V alpha = (V)s_alpha;
     acc = 0.0;
     for (int k = threadIdx.x; k < 3 * nr; k += CNT) {
       x[k] += alpha * pfull[3 * r0 + k];
-      const T rk = r[k] - alpha * Ap[k];
+      const V rk = r[k] - alpha * Ap[k];
       r[k] = rk;
-      const T zk = rk / dg[k];
+      const V zk = rk / dg[k];
       for (int dst = 0; dst < cl; ++dst) cluster.map_shared_rank(zfull, dst)[3 * r0 + k] = zk;
       acc += (double)rk * (double)zk;
     }
@@ -1058,11 +1066,11 @@ __global__ void __launch_bounds__(CNT) k_coarse_pcg_cluster(int R, const int *__
       s_stop = (sqrt(fmax(rz, 0.0)) <= kk * bn || it >= max_iter) ? 1 : 0;
     }
     __syncthreads();
-    const T beta = (T)s_beta;
+    const V beta = (V)s_beta;
     for (int k = threadIdx.x; k < 3 * R; k += CNT) pfull[k] = zfull[k] + beta * pfull[k];
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < 3 * nr; k += CNT) xout[3 * r0 + k] = x[k];
+  for (int k = threadIdx.x; k < 3 * nr; k += CNT) xout[3 * r0 + k] = (T)x[k];
   if (rank == 0 && threadIdx.x == 0) {
     int k = *log_idx;
     if (k < log_cap) log[k] = it;
@@ -1237,6 +1245,7 @@ int persistent_blocks() {
 // a few dozen rows, and more once a color's FP64 rows outgrow 16 SMs (about a
 // hundred rows), hence the row limit.
 constexpr int CLUSTER_SWEEP_ROWS = 64;
+constexpr int CLUSTER_SWEEP_ROWS_FP32 = 256;   // FP32 rows do not load the FP64 pipe
 template <class T>
 int sweep_cluster_size() {
   static std::atomic<int> cached{-1};
@@ -1274,7 +1283,8 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
   // levels whose colors have at most CLUSTER_SWEEP_ROWS rows: one cluster,
   // hardware cluster barriers between colors (flag bit 6 turns this off)
   const int CLR = sweep_cluster_size<T>();
-  if (CLR > 0 && !(s.opts.flags & 64) && max_rows <= std::min(CLUSTER_SWEEP_ROWS, CLR * SW_WARPS)) {
+  const int row_limit = sizeof(T) == 4 ? CLUSTER_SWEEP_ROWS_FP32 : CLUSTER_SWEEP_ROWS;
+  if (CLR > 0 && !(s.opts.flags & 64) && max_rows <= std::min(row_limit, CLR * SW_WARPS)) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CLR);
     cfg.blockDim = dim3(SW_NT);
@@ -1288,7 +1298,7 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
     cfg.numAttrs = 1;
     HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T, false, true>, plan, (const int4 *)t.color_rec.p,
                                 (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
-                                V.u.p, (unsigned *)nullptr, s.errflag.p));
+                                V.u.p, (unsigned *)nullptr, s.errflag.p, s.spin_limit));
     note_launch("k_sgs_persistent");
     return;
   }
@@ -1308,11 +1318,11 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
   if (max_rows > G * SW_WARPS)
     HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T, true>, plan, (const int4 *)t.color_rec.p,
                                 (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
-                                V.u.p, bar, s.errflag.p));
+                                V.u.p, bar, s.errflag.p, s.spin_limit));
   else
     HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T, false>, plan, (const int4 *)t.color_rec.p,
                                 (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
-                                V.u.p, bar, s.errflag.p));
+                                V.u.p, bar, s.errflag.p, s.spin_limit));
   note_launch("k_sgs_persistent");
 }
 
@@ -1384,9 +1394,9 @@ void plan_cluster(Scene &s, Hier<T> &h, int m) {
   // set once, to the maximum: scenes planned on other threads launch the same kernel
   static std::once_flag once;
   std::call_once(once, [] {
-    HOT_CUDA(cudaFuncSetAttribute(k_coarse_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HOT_CUDA(cudaFuncSetAttribute(k_coarse_pcg_cluster<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)CL_SMEM_MAX));
-    if (cudaFuncSetAttribute(k_coarse_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+    if (cudaFuncSetAttribute(k_coarse_pcg_cluster<T, double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
         cudaSuccess)
       cudaGetLastError();
   });
@@ -1406,8 +1416,9 @@ void plan_cluster(Scene &s, Hier<T> &h, int m) {
       rows_max = std::max(rows_max, bounds[c + 1] - bounds[c]);
       nb_max = std::max(nb_max, rp[bounds[c + 1]] - rp[bounds[c]]);
     }
+    // vectors and the staged matrix values in FP64 whatever the hierarchy's precision
     const size_t bytes = 2 * CLMAX * sizeof(double) +
-                         sizeof(T) * (6 * (size_t)R + 4 * 3 * (size_t)rows_max + 9 * (size_t)nb_max) +
+                         sizeof(double) * (6 * (size_t)R + 4 * 3 * (size_t)rows_max + 9 * (size_t)nb_max) +
                          sizeof(int) * ((size_t)rows_max + 1 + nb_max) + 64;
     if (bytes > CL_SMEM_MAX) continue;
     cudaLaunchConfig_t cfg = {};
@@ -1422,7 +1433,8 @@ void plan_cluster(Scene &s, Hier<T> &h, int m) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_pcg_cluster<T>, &cfg) != cudaSuccess || nclusters < 1) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_pcg_cluster<T, double>, &cfg) != cudaSuccess ||
+        nclusters < 1) {
       cudaGetLastError();
       continue;
     }
@@ -1441,11 +1453,16 @@ void coarse_solve(Scene &s, Hier<T> &h, int m) {
   Vals<T> &V = h.L[m];
   int64_t nn = t.n;
   const int cap = (int)h.cg_log.cap;
-  // float32 coarse matrices of stiff scenes can lose definiteness to rounding,
-  // where CG stalls short of its tolerance: cap float32 runs at 100 iterations
-  const int max_iter = s.opts.max_coarse_cg > 0 ? s.opts.max_coarse_cg
-                                                : (int)(sizeof(T) == 4 ? std::min<int64_t>(3 * nn, 100) : 3 * nn);
-  if (h.cl_smem > 0 && !(s.opts.flags & 2)) {
+  // Float32 coarse matrices of stiff scenes can lose definiteness to rounding,
+  // where CG stalls short of its tolerance.  The cluster solver works in FP64
+  // on the float32 matrix (its level is a few hundred rows in shared memory),
+  // capped at 200 iterations; the cooperative fallback computes in float32,
+  // capped at 100.
+  const bool cluster = h.cl_smem > 0 && !(s.opts.flags & 2);
+  const int max_iter = s.opts.max_coarse_cg > 0
+                           ? s.opts.max_coarse_cg
+                           : (int)(sizeof(T) == 4 ? std::min<int64_t>(3 * nn, cluster ? 200 : 100) : 3 * nn);
+  if (cluster) {
     ClusterPlan plan;
     for (int c = 0; c <= h.cl_size; ++c) plan.bounds[c] = h.cl_bounds[c];
     cudaLaunchConfig_t cfg = {};
@@ -1461,7 +1478,7 @@ void coarse_solve(Scene &s, Hier<T> &h, int m) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     ProfScope prof_(s, "coarse_pcg");
-    HOT_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_pcg_cluster<T>, (int)nn, (const int *)t.row_ptr.p,
+    HOT_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_pcg_cluster<T, double>, (int)nn, (const int *)t.row_ptr.p,
                                 (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.diag.p, (const T *)V.b.p,
                                 V.u.p, plan, h.cl_rows_max, h.cl_nb_max, s.opts.eps, max_iter, h.cg_log.p,
                                 h.cg_log.p + (cap - 1), cap - 1));
@@ -1487,7 +1504,7 @@ void coarse_solve(Scene &s, Hier<T> &h, int m) {
   HOT_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_pcg<T>, nn, (const int *)t.row_ptr.p, (const int *)t.cols.p,
                               (const T *)V.vals.p, (const T *)V.diag.p, (const T *)V.b.p, V.u.p, h.r.p, h.z.p,
                               h.p.p, h.Ap.p, h.part.p, h.bar.p, h.cg_log.p, h.cg_log.p + (cap - 1), cap - 1,
-                              s.errflag.p, tau, max_iter));
+                              s.errflag.p, tau, max_iter, s.spin_limit));
   note_launch("k_coarse_pcg");
 }
 

@@ -1,13 +1,13 @@
 // Allocation-free evaluation of the particles' elastic energy.
 //
 // Some callers cannot allocate device memory at the moment they need this
-// value: code that runs while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a stream operation and is refused or breaks the
-// capture), real-time loops that must not hit the implicit device
-// synchronisation of cudaMalloc/cudaFree, and hosts whose memory budget is
-// fixed up front by their own pool.  This file serves them with one entry
-// point whose only scratch is a fixed array in the library's own device
-// memory, reserved when the library is loaded.
+// value: real-time loops that must not hit the implicit device
+// synchronisation of cudaMalloc/cudaFree, hosts whose device memory budget is
+// fixed up front by their own pool, and code paths that may not enter an
+// allocator at all.  This file serves them with one entry point whose only
+// scratch is a fixed array in the library's own device memory, reserved on a
+// device when the library's module is first loaded there (with lazy module
+// loading, at the first use of the module on that device).
 #include <mutex>
 
 #include "internal.h"
@@ -68,21 +68,71 @@ __global__ void k_energy_total_noalloc(const double *__restrict__ partial, int n
   }
 }
 
-// device address of the scratch array, looked up once per device
-std::mutex g_na_mutex;
-double *g_na_ptr[64] = {nullptr};
+// Device address of the scratch array, looked up once per CUDA context.  The
+// cache is keyed on the context's unique id (cuCtxGetId, reached through the
+// runtime's driver entry points, so the library needs no link to the driver
+// library): after a cudaDeviceReset the device gets a new primary context,
+// the module is loaded again and the array is looked up again, so no address
+// from a destroyed context is ever used.  Where the driver entry points are
+// not available the key falls back to the device ordinal.
+using PfnCtxGetCurrent = int (*)(void **ctx);
+using PfnCtxGetId = int (*)(void *ctx, unsigned long long *id);
 
-double *scratch_for_current_device() {
+std::mutex g_na_mutex;
+std::once_flag g_na_once;
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+struct NaEntry {
+  unsigned long long key;
+  double *ptr;
+};
+constexpr int NA_CACHE = 64;   // contexts remembered (fixed size: no allocation here either)
+NaEntry g_na_cache[NA_CACHE];
+int g_na_cached = 0;
+
+void resolve_driver_entry_points() {
+  void *f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+  f = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f);
+  cudaGetLastError();
+}
+
+// key of the current context: its unique id, else (1 << 63) | device ordinal
+bool current_context_key(unsigned long long &key) {
+  if (g_ctx_get_current && g_ctx_get_id) {
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) == 0 && ctx && g_ctx_get_id(ctx, &id) == 0) {
+      key = id;
+      return true;
+    }
+    return false;   // no current context yet
+  }
   int dev = 0;
   check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
-  if (dev < 0 || dev >= 64) fail(MPM_ERR_INVALID_ARG, "device ordinal out of range");
+  key = (1ull << 63) | (unsigned long long)dev;
+  return true;
+}
+
+double *scratch_for_current_device() {
+  std::call_once(g_na_once, resolve_driver_entry_points);
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    double *p = nullptr;
-    check_cuda(cudaGetSymbolAddress((void **)&p, g_noalloc_scratch), "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_na_ptr[dev] = p;
-  }
-  return g_na_ptr[dev];
+  unsigned long long key = 0;
+  const bool have_key = current_context_key(key);
+  if (have_key)
+    for (int k = 0; k < g_na_cached; ++k)
+      if (g_na_cache[k].key == key) return g_na_cache[k].ptr;
+  double *p = nullptr;   // (this lookup makes the device's context current if none was)
+  check_cuda(cudaGetSymbolAddress((void **)&p, g_noalloc_scratch), "cudaGetSymbolAddress(g_noalloc_scratch)");
+  if (!have_key && !current_context_key(key)) return p;   // not cached: looked up again next call
+  if (g_na_cached < NA_CACHE) g_na_cache[g_na_cached++] = NaEntry{key, p};
+  return p;
 }
 
 }  // namespace

@@ -31,7 +31,7 @@ EXPORTED = ["mpm_set_allocator", "mpm_create_scene", "mpm_destroy_scene", "mpm_l
             "mpm_scene_footprint", "mpm_step_batch", "mpm_profile", "mpm_profile_read",
             "mpm_kernel_launch_count", "mpm_particle_energy_noalloc", "mpm_server_create",
             "mpm_server_submit", "mpm_server_poll", "mpm_server_info", "mpm_server_destroy",
-            "mpm_probe_fp64_fma"]
+            "mpm_probe_fp64_fma", "mpm_set_wait_limit"]
 
 
 class mpm_material(C.Structure):
@@ -268,6 +268,10 @@ class HotScene:
         except Exception:
             pass
 
+    def set_wait_limit(self, polls: int):
+        """Poll limit of the scene's device-side barrier waits (default 2^24)."""
+        self._check(self.lib.mpm_set_wait_limit(self.h, C.c_int64(int(polls))))
+
     def set_options(self, opts):
         self.opts = opts
         o = opts_struct(opts)
@@ -407,8 +411,8 @@ def particle_energy_noalloc(F_dev: int, vol_dev: int, mat_dev: int, materials, n
                             out_dev: Optional[int] = None, stream: int = 0) -> Optional[float]:
     """Elastic energy of n particles from device arrays (F n x 9, vol n,
     material ids n) without any device allocation: for callers that cannot
-    allocate (during graph capture, in allocation-free loops).  Returns the
-    value (host result) or None when out_dev (a device double*) is given."""
+    allocate (allocation-free loops, fixed device-memory budgets).  Returns
+    the value (host result) or None when out_dev (a device double*) is given."""
     lib = load()
     mats = (mpm_material * len(materials))(*[
         mpm_material(m.E, m.nu, m.rho, m.yield_stress, m.model, m.plasticity) for m in materials])

@@ -91,3 +91,50 @@ def test_iteration_cap_reports_not_converged_and_advances(hot):
     x1 = g.get_state()["x"]
     assert np.all(np.isfinite(x1)) and not np.array_equal(x1, x0)
     g.close()
+
+
+def test_device_wait_timeout_is_reported_and_scene_recovers(hot):
+    """Every device-side barrier wait is bounded.  With the poll limit cut to
+    one poll, the cooperative Gauss-Seidel sweeps and the cooperative coarsest
+    PCG (flag bits 6 and 1: grid barriers on every level) give up waiting,
+    record the timeout and return; mpm_apply_vcycle reports MPM_ERR_TIMEOUT.
+    No index leaves its buffer, so the early exits race but cannot fault.
+    With the default limit back, the same scene applies a V-cycle that the
+    oracle reproduces and takes a step whose result the oracle replays."""
+    from oracle import hot_oracle as O
+    sc = scenes.two_bars_scene(seed=4, res=64, width=6, length=14, gap=8, E_a=1e5, E_b=1e8)
+    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, flags=64 | 2)
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    g.build_hierarchy()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, O.step_dt(sc, opts))
+    b = np.random.default_rng(6).normal(size=(prob.n, 3))
+    g.set_wait_limit(1)
+    timed_out = False
+    for _ in range(3):
+        try:
+            g.vcycle(b)
+        except hot.HotError as e:
+            assert e.code == 10 and "timed out" in str(e)     # MPM_ERR_TIMEOUT
+            timed_out = True
+            break
+    assert timed_out
+    with pytest.raises(hot.HotError):
+        g.set_wait_limit(0)
+    g.set_wait_limit(1 << 24)
+    u, its = g.vcycle(b)
+    L = O.build_hierarchy(og.coords, prob.hessian(), prob.hessian_pattern(), opts.levels)
+    vc = O.VCycle(L, og.fixed, opts.eps, opts.max_coarse_cg)
+    vc.forced = [its]
+    uo = vc(b)
+    assert np.abs(u - uo).max() <= 1e-9 * np.abs(uo).max()
+    st = g.solve()
+    assert st["status"] == 0
+    tr = g.trace()
+    dv = g.grid()["dv"]
+    g.close()
+    rep = O.Trace(iters=tr["iters"], alphas=tr["alphas"], ls_trials=tr["ls_trials"], cg_counts=tr["cg_counts"],
+                  skipped=tr["skipped"], fallback=tr["fallback"])
+    dvo, _ = O.hot_solve(O.Problem(sc, og, st["dt"]), opts, replay=rep)
+    assert np.abs(dv - dvo).max() <= 1e-9 * np.abs(dvo).max()

@@ -185,3 +185,70 @@ def test_fullsize_mixed_2m_converges_to_oracle_tolerance():
     ref = O.g2p(sc, og, og.v + gd["dv"], prob.dt)
     assert rel(out["x"], ref.x) < 1e-12
     g.close()
+
+
+@pytest.fixture(scope="module")
+def later():
+    """The benchmark scene twelve steps in (the trajectory bench.py times:
+    HOT with the hierarchy refreshed every 5 iterations), stepped by the GPU
+    from seed 0; the oracle gets the GPU's particle state."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1911_07913_gb300 import hot
+    opts = scenes.SolverOptions(**{**OPTS.__dict__, "refresh_every": 5})
+    sc = scenes.two_bars_scene(seed=0)
+    stream = torch.cuda.Stream()
+    g = hot.HotScene(sc, opts, stream=stream.cuda_stream)
+    for _ in range(12):
+        assert g.step()["status"] == 0
+    st = g.get_state()
+    sc12 = sc.copy()
+    sc12.x, sc12.v, sc12.F, sc12.C = st["x"], st["v"], st["F"], st["C"]
+    g.p2g()
+    og = O.p2g(sc12)
+    prob = O.Problem(sc12, og, O.step_dt(sc12, opts))
+    yield sc12, g, og, prob, opts
+    g.close()
+
+
+def test_later_state_p2g_energy_gradient(later):
+    """Twelve steps into the run: active nodes and Dirichlet flags bit-exact,
+    m, v, xi, E and grad E at a random dv as tight as at step 0."""
+    sc, g, og, prob, opts = later
+    gd = g.grid()
+    assert np.array_equal(gd["coords"], og.coords.astype(np.int32))
+    assert np.array_equal(gd["fixed"], og.fixed)
+    assert rel(gd["m"], og.m) < 1e-12 and rel(gd["v"], og.v) < 1e-12 and rel(gd["xi"], og.xi) < 1e-12
+    rng = np.random.default_rng(15)
+    dv = 0.01 * rng.normal(size=(prob.n, 3))
+    dv[og.fixed] = 0.0
+    assert abs(g.energy(dv) - prob.energy(dv)) <= 1e-12 * abs(prob.energy(dv))
+    assert rel(g.gradient(dv), prob.gradient(dv)) < 1e-11
+
+
+def test_later_state_vcycle_and_step(later):
+    """At the same state: one V-cycle against the oracle's V-cycle on the
+    GPU's hierarchy, then a solve whose result the oracle's CN test accepts."""
+    sc, g, og, prob, opts = later
+    g.build_hierarchy()
+    mats = [g.hessian(m) for m in range(opts.levels)]
+    levels = []
+    for m, h in enumerate(mats):
+        coords = h["coords"].astype(np.int64)
+        Hm = gpu_level_matrix(h)
+        R = O.restriction(coords, mats[m + 1]["coords"].astype(np.int64)) if m + 1 < len(mats) else None
+        pat = sp.csr_matrix((np.ones(h["cols"].size), h["cols"], h["row_ptr"]), shape=(coords.shape[0],) * 2)
+        levels.append(O.Level(coords=coords, H=Hm, pattern=pat, R=R, colors=O.node_colors(coords),
+                              Dblk=O.diag_blocks(Hm, coords.shape[0])))
+    b = np.random.default_rng(16).normal(size=(prob.n, 3))
+    u, its = g.vcycle(b)
+    vc = O.VCycle(levels, og.fixed, opts.eps, opts.max_coarse_cg)
+    vc.forced = [its]
+    assert rel(u, vc(b)) < 1e-9
+    st = g.solve()
+    assert st["status"] == 0
+    gd = g.grid()
+    nrm, nfree = prob.cn_norm(prob.gradient(gd["dv"]))
+    assert nrm <= opts.eps * np.sqrt(nfree) * (1 + 1e-6)
+    assert prob.energy(gd["dv"]) < prob.energy(np.zeros_like(gd["dv"]))

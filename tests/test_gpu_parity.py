@@ -528,3 +528,35 @@ def test_server_results_match_alone_and_admission(hot):
     srv.close()
     for g in gs:
         g.close()
+
+
+@pytest.mark.parametrize("name", ["cube8k_fcr", "bars_cyl"])
+def test_mixed_step_error_against_fp64_oracle(hot, name):
+    """Mixed precision (FP32 Hessian, smoother and coarse-level storage; FP64
+    energy, gradient, L-BFGS dots and CN test): one step from the scene's
+    start reaches the tolerance by the FP64 oracle's own test, and its result
+    differs from the FP64 oracle's own converged step by no more than the
+    tolerance allows: particle positions within 1e-6 relative (of |x|) and
+    grid v^{n+1} within 1e-3 relative (infinity norms)."""
+    sc, opts = SCENES[name]
+    opts = scenes.SolverOptions(**{**opts.__dict__, "precision": 1})
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    st = g.solve()
+    assert st["status"] == 0
+    gd = g.grid()
+    g.g2p()
+    out = g.get_state()
+    g.close()
+    og = O.p2g(sc)
+    prob = O.Problem(sc, og, st["dt"])
+    gr = prob.gradient(gd["dv"])
+    if opts.cn_mode == 0:
+        nrm, nfree = prob.cn_norm(gr)
+        assert nrm <= opts.eps * np.sqrt(nfree) * (1 + 1e-6)
+    else:
+        assert np.sqrt(np.sum(gr * gr)) <= opts.eps * np.sqrt(np.sum(prob.gradient(0 * gr) ** 2)) * (1 + 1e-6)
+    ref, info = O.hot_step(sc, scenes.SolverOptions(**{**opts.__dict__, "precision": 0}))
+    assert info["trace"].status == "ok"
+    assert rel(og.v + gd["dv"], info["v_new"]) < 1e-3
+    assert rel(out["x"], ref.x) < 1e-6

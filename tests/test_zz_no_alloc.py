@@ -1,10 +1,12 @@
 """The allocation-free energy entry point (mpm_particle_energy_noalloc).
 
 It serves callers that cannot allocate device memory when they need the
-value -- during CUDA-graph capture, or in loops that must avoid the implicit
-synchronisation of cudaMalloc/cudaFree.  Checked through the C ABI against
-the scene-based mpm_eval_energy on the same particles, twice in a row (the
-two calls share the library's fixed scratch array)."""
+value -- loops that must avoid the implicit synchronisation of
+cudaMalloc/cudaFree, hosts whose device memory is a fixed budget, code that
+may not enter an allocator.  Checked through the C ABI against the
+scene-based mpm_eval_energy on the same particles, twice in a row (the two
+calls share the library's fixed scratch array), plus its edge cases: no
+particles, no material ids, an id outside the table."""
 import numpy as np
 import pytest
 
@@ -58,3 +60,25 @@ def test_noalloc_rejects_oversized_input():
     with pytest.raises(hot.HotError) as e:
         hot.particle_energy_noalloc(0, 0, 0, mats, 134_217_729)
     assert e.value.code == 1 and "limit" in str(e.value)
+
+
+def test_noalloc_edge_cases():
+    """n = 0 gives 0 (only the total kernel runs, over zero partials); NULL
+    material ids mean material 0; an id outside the table makes the sum NaN."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1911_07913_gb300 import hot
+    sc = _scene(0)
+    dev = torch.device("cuda:0")
+    F = torch.tensor(sc.F.reshape(-1, 9), dtype=torch.float64, device=dev)
+    vol = torch.tensor(sc.vol, dtype=torch.float64, device=dev)
+    mat = torch.zeros(sc.n, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    assert hot.particle_energy_noalloc(F.data_ptr(), vol.data_ptr(), mat.data_ptr(), sc.materials, 0) == 0.0
+    with_ids = hot.particle_energy_noalloc(F.data_ptr(), vol.data_ptr(), mat.data_ptr(), sc.materials, sc.n)
+    no_ids = hot.particle_energy_noalloc(F.data_ptr(), vol.data_ptr(), 0, sc.materials, sc.n)
+    assert no_ids == with_ids and with_ids > 0.0
+    mat[sc.n // 2] = 5            # one material in the table
+    torch.cuda.synchronize()
+    assert np.isnan(hot.particle_energy_noalloc(F.data_ptr(), vol.data_ptr(), mat.data_ptr(), sc.materials, sc.n))
