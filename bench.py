@@ -403,16 +403,17 @@ def run_batching(seed, steps, count=64):
     import torch
     from paper_1911_07913_gb300 import hot
     scs = scenes.batch_scenes(seed=seed, count=count)
-    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500)
+    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500, refresh_every=REFRESH)
     gs = [hot.HotScene(sc, opts) for sc in scs]
     hot.step_batch(gs, check=False)       # warm-up: allocations, first hierarchy
     tuned = hot.batch_autotune(gs, 1)     # launch configuration: 6 more (ordinary) steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    iters = []
+    iters, conv = [], 0
     for _ in range(steps):
         st = hot.step_batch(gs, check=False)
         iters.append(sum(x["iters"] for x in st))
+        conv += sum(1 for x in st if x["status"] == 0)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     n_total = sum(sc.n for sc in scs)
@@ -428,7 +429,7 @@ def run_batching(seed, steps, count=64):
             "ms_per_batch_step": 1e3 * secs / steps, "sequential_value": n_total / seq,
             "speedup_vs_sequential": (n_total * steps / secs) / (n_total / seq),
             "autotuned": tuned,
-            "lbfgs_iters_per_batch_step": iters,
+            "lbfgs_iters_per_batch_step": iters, "converged_scene_steps": conv, "scene_steps": steps * count,
             "config": "64 boxes, N_p log-uniform 5k-200k, grids 64^3/96^3/128^3, FCR E log-uniform 1e4-1e8, "
                       "half von Mises (yield 1e4 Pa), FP32 preconditioner, 3 levels, CN eps 1e-7, CFL dt"}
 
@@ -471,72 +472,93 @@ def run_solvers(seed, steps=4, warmup=2):
     return out
 
 
-def run_serving(seed, count=256, requests=512, workers=12, budget_gb=150.0, load=0.8, flags=0):
-    """Resident scenes behind the continuous-batching server: a saturating
-    burst measures capacity, then a Poisson stream at `load` of that capacity
-    measures request latency (arrival -> result).  `flags`: the launch
-    configuration the batch autotuner chose for the same kind of workload."""
-    import torch
-    from paper_1911_07913_gb300 import hot
-    scs = scenes.serving_scenes(seed=seed, count=count)
-    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500, flags=flags)
-    gs = [hot.HotScene(sc, opts) for sc in scs]
-    srv = hot.StepServer(budget_bytes=int(budget_gb * (1 << 30)), n_workers=workers)
-    for i, g in enumerate(gs):           # first step of every scene: buffers become resident
-        srv.submit(g, i)
-    while srv.poll(wait=True) is not None:
-        pass
-    footprint = sum(g.footprint() for g in gs)
-    rng = np.random.default_rng(seed + 1)
-    # capacity: a burst of requests
+def _serve_phase(srv, gs, scs, rng, count, requests, load, cap_rate=None, rid0=0):
+    """A saturating burst (capacity), or Poisson arrivals at `load` x the
+    given capacity; returns (latencies in ms, wall s, particle-steps)."""
     pick = rng.integers(count, size=requests)
-    t0 = time.perf_counter()
-    for r, i in enumerate(pick):
-        srv.submit(gs[i], r)
-    done = 0
-    while srv.poll(wait=True) is not None:
-        done += 1
-    cap_s = time.perf_counter() - t0
-    cap_rate = requests / cap_s
-    cap_particles = sum(scs[i].n for i in pick) / cap_s
-    # Poisson arrivals at a fraction of capacity
-    rate = load * cap_rate
-    pick = rng.integers(count, size=requests)
-    gaps = rng.exponential(1.0 / rate, size=requests)
     lat = []
     t0 = time.perf_counter()
-    t_next = t0
-    for r, i in enumerate(pick):
-        t_next += gaps[r]
-        while True:
-            now = time.perf_counter()
-            if now >= t_next:
-                break
-            out = srv.poll(wait=False)
-            if out is not None:
-                lat.append(out["latency_s"])
-            else:
-                time.sleep(min(5e-4, t_next - now))
-        srv.submit(gs[i], requests + r)
+    if cap_rate is None:
+        for r, i in enumerate(pick):
+            srv.submit(gs[i], rid0 + r)
+    else:
+        gaps = rng.exponential(1.0 / (load * cap_rate), size=requests)
+        t_next = t0
+        for r, i in enumerate(pick):
+            t_next += gaps[r]
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                out = srv.poll(wait=False)
+                if out is not None:
+                    lat.append(out["latency_s"])
+                else:
+                    time.sleep(min(5e-4, t_next - now))
+            srv.submit(gs[i], rid0 + r)
+    bad = 0
     while True:
         out = srv.poll(wait=True)
         if out is None:
             break
         lat.append(out["latency_s"])
+        bad += out["code"] != 0
     wall = time.perf_counter() - t0
-    info = srv.info()
+    return np.array(lat) * 1e3, wall, sum(scs[i].n for i in pick), bad
+
+
+def run_serving(seed, count=256, requests=512, workers=12, budget_gb=150.0, load=0.8, flags=0,
+                bind_fraction=0.25):
+    """Resident scenes behind the continuous-batching server.  For each budget
+    -- the configured 150 GB, and one at `bind_fraction` of the scenes' summed
+    peak footprint, where residency admission binds (idle scenes are parked to
+    host memory, requests wait for memory) -- a saturating burst measures
+    capacity, then a Poisson stream at `load` of that capacity measures
+    request latency (arrival -> result).  `flags`: the launch configuration
+    the batch autotuner chose for the same kind of workload."""
+    import torch
+    from paper_1911_07913_gb300 import hot
+    scs = scenes.serving_scenes(seed=seed, count=count)
+    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500, flags=flags,
+                                refresh_every=REFRESH)
+    gs = [hot.HotScene(sc, opts) for sc in scs]
+    srv = hot.StepServer(budget_bytes=int(budget_gb * (1 << 30)), n_workers=workers)
+    for i, g in enumerate(gs):           # first step of every scene: its footprint becomes known
+        srv.submit(g, i)
+    while srv.poll(wait=True) is not None:
+        pass
     srv.close()
+    peak_total = sum(g.residency()["peak_bytes"] for g in gs)
+    out = {"unit": UNIT, "scenes": count, "resident_particles": sum(sc.n for sc in scs),
+           "scenes_peak_footprint_gb": peak_total / 2 ** 30, "requests": requests, "workers": workers,
+           "launch_flags": flags, "offered_load": load,
+           "config": "scenes with N_p lognormal (median 50k, sigma 1, <= 1M), E log-uniform 1e4-1e9, FCR/NH, "
+                     f"every third von Mises, FP32 preconditioner, 3 levels, CN eps 1e-7, refresh every {REFRESH}; "
+                     "Poisson arrivals"}
+    rng = np.random.default_rng(seed + 1)
+    for tag, budget in (("configured", budget_gb * (1 << 30)), ("binding", bind_fraction * peak_total)):
+        if tag == "binding":
+            for g in gs:             # start from nothing resident: the server decides what comes back
+                g.park()
+        srv = hot.StepServer(budget_bytes=int(budget), n_workers=workers)
+        lat_b, wall_b, ps_b, bad_b = _serve_phase(srv, gs, scs, rng, count, requests, load)
+        cap_rate = requests / wall_b
+        lat, wall, ps, bad = _serve_phase(srv, gs, scs, rng, count, requests, load, cap_rate, rid0=requests)
+        info = srv.info()
+        srv.close()
+        out[tag] = {"budget_gb": budget / 2 ** 30, "value": ps / wall,
+                    "capacity_requests_per_s": cap_rate, "capacity_particle_steps_per_s": ps_b / wall_b,
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "mean_ms": float(lat.mean()), "failed_requests": int(bad + bad_b),
+                    "peak_resident_gb": info["peak_resident_bytes"] / 2 ** 30,
+                    "peak_in_flight_gb": info["peak_in_flight_bytes"] / 2 ** 30,
+                    "parks": info["parks"], "unparks": info["unparks"], "deferred_requests": info["deferred"],
+                    "admission_binds": bool(info["parks"] > 0 or info["deferred"] > 0)}
+    out["value"] = out["configured"]["value"]
+    out["p50_ms"], out["p99_ms"] = out["configured"]["p50_ms"], out["configured"]["p99_ms"]
     for g in gs:
         g.close()
-    lat = np.array(lat) * 1e3
-    return {"value": sum(scs[i].n for i in pick) / wall, "unit": UNIT, "scenes": count,
-            "resident_particles": sum(sc.n for sc in scs), "resident_footprint_gb": footprint / 2 ** 30,
-            "requests": requests, "workers": workers, "launch_flags": flags, "budget_gb": budget_gb,
-            "capacity_requests_per_s": cap_rate, "capacity_particle_steps_per_s": cap_particles,
-            "offered_load": load, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "peak_in_flight_gb": info["peak_in_flight_bytes"] / 2 ** 30,
-            "config": "resident scenes, N_p lognormal (median 50k, sigma 1, <= 1M), E log-uniform 1e4-1e9, FCR/NH, "
-                      "every third von Mises, FP32 preconditioner, 3 levels, CN eps 1e-7; Poisson arrivals"}
+    return out
 
 
 # --------------------------------------------------------------------------- host oracle

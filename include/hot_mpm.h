@@ -310,15 +310,34 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
 mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int32_t *flags_out,
                               int32_t *workers_out, double *rate_out, int32_t *steps_run_out);
 
-/* Continuous-batching step server (serving many resident scenes).  Requests
- * (one implicit step of a scene each) queue in FIFO order and are admitted
- * when a worker is free, the scene is not already being stepped, and the
- * summed device footprint of the scenes in flight plus this scene's stays
- * within budget_bytes (a lone request is always admitted).  Each worker
- * thread steps its scene with mpm_step on the scene's own stream, so admitted
- * requests overlap on the GPU.  Scenes stay resident between requests (their
- * grids, hierarchy buffers and L-BFGS storage remain allocated); create them
- * with cuda_stream = NULL so that each gets its own stream.
+/* Residency of a scene's device memory.  park: copy the particle state
+ * (positions, velocities, F, C, volumes, masses, material and original ids)
+ * to host memory and release every device buffer of the scene (grid,
+ * hierarchy and solver storage are rebuilt by the next step, as Alg. 3 builds
+ * them per step anyway).  unpark: allocate and copy it back; mpm_p2g,
+ * mpm_step, mpm_get_state and mpm_set_state unpark a parked scene by
+ * themselves.  residency: *parked (0/1) and *peak_bytes, the largest device
+ * footprint the scene has had (what it needs when brought back).  The paper
+ * has no counterpart (serving many scenes).  Errors: INVALID_ARG, OOM, CUDA. */
+mpm_status mpm_scene_park(mpm_scene_t s);
+mpm_status mpm_scene_unpark(mpm_scene_t s);
+mpm_status mpm_scene_residency(mpm_scene_t s, int32_t *parked, int64_t *peak_bytes);
+
+/* Continuous-batching step server (serving many scenes) with residency
+ * admission.  Requests (one implicit step of a scene each) queue in FIFO
+ * order.  The server manages the device memory of every scene submitted to
+ * it: the summed footprint of its resident scenes stays within budget_bytes.
+ * A request is admitted when a worker is free, its scene is not already
+ * being stepped, and room can be made for it: a parked scene needs its peak
+ * footprint, a resident one the growth back to its peak; to make room, idle
+ * resident scenes are parked, least recently stepped first.  A request for
+ * which no room can be made waits while other work is in flight; a lone
+ * request is always admitted (so an over-budget mix cannot stall the queue).
+ * A scene's first step may overshoot (its peak is unknown before it).  Each
+ * worker thread steps its scene with mpm_step on the scene's own stream, so
+ * admitted requests overlap on the GPU; create scenes with cuda_stream = NULL
+ * so that each gets its own stream, and do not use a scene elsewhere while
+ * the server manages it.
  *   submit: MPM_ERR_ADMISSION if the scene alone exceeds the budget.
  *   poll:   *request_id = -1 when nothing has finished (wait = 0) or nothing
  *           is pending (wait = 1); latency = submit -> finish, queue = submit
@@ -331,6 +350,11 @@ mpm_status mpm_server_poll(mpm_server_t server, int32_t wait, int64_t *request_i
                            double *latency_s, double *queue_s, int32_t *step_status);
 mpm_status mpm_server_info(mpm_server_t server, int64_t *queued, int64_t *in_flight, int64_t *in_flight_bytes,
                            int64_t *peak_in_flight_bytes);
+/* resident bytes of the managed scenes now and at their peak (sampled after
+ * each request), scenes parked and brought back so far, and requests that
+ * had to wait for device memory. */
+mpm_status mpm_server_residency(mpm_server_t server, int64_t *resident_bytes, int64_t *peak_resident_bytes,
+                                int64_t *parks, int64_t *unparks, int64_t *deferred);
 mpm_status mpm_server_destroy(mpm_server_t server);
 
 /* FP64 FMA throughput of the current device in TFLOP/s (2 flop per FMA),

@@ -145,6 +145,82 @@ void Scene::release() {
 
 namespace {
 
+// material table, boundary boxes and the status word on the device (scene
+// creation, and again when a parked scene comes back)
+void upload_tables(Scene &s) {
+  std::vector<MatParams> mt(s.mats.size());
+  for (size_t k = 0; k < s.mats.size(); ++k) {
+    double E = s.mats[k].E, nu = s.mats[k].nu;
+    mt[k].mu = E / (2.0 * (1.0 + nu));
+    mt[k].lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    mt[k].xi = std::sqrt(3.0 * (2.0 * mt[k].mu + mt[k].lam) * (2.0 * mt[k].mu + mt[k].lam) +
+                         6.0 * mt[k].lam * mt[k].lam);
+    mt[k].model = s.mats[k].model;
+    mt[k].plastic = s.mats[k].plasticity;
+    mt[k].yield = s.mats[k].yield_stress;
+  }
+  s.mat_table.ensure(mt.size(), 1.0);
+  HOT_CUDA(cudaMemcpyAsync(s.mat_table.p, mt.data(), sizeof(MatParams) * mt.size(), cudaMemcpyHostToDevice, s.st));
+  s.bc_dev.ensure(std::max<size_t>(1, s.bcs.size()), 1.0);
+  if (!s.bcs.empty())
+    HOT_CUDA(cudaMemcpyAsync(s.bc_dev.p, s.bcs.data(), sizeof(mpm_bc) * s.bcs.size(), cudaMemcpyHostToDevice, s.st));
+  s.errflag.ensure(4, 1.0);
+  HOT_CUDA(cudaMemsetAsync(s.errflag.p, 0, sizeof(int) * 4, s.st));
+  HOT_CUDA(cudaStreamSynchronize(s.st));   // the host vectors above are released on return
+}
+
+}  // namespace
+
+void park_scene(Scene &s) {
+  if (s.parked) return;
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  s.peak_bytes = std::max(s.peak_bytes, s.bytes());
+  const size_t np = (size_t)s.np;
+  s.host_pd.resize((size_t)PF_COUNT * np);
+  s.host_pmat.resize(np);
+  s.host_pid.resize(np);
+  if (np > 0) {
+    HOT_CUDA(cudaMemcpyAsync(s.host_pd.data(), s.pd.p, sizeof(double) * PF_COUNT * np, cudaMemcpyDeviceToHost, s.st));
+    HOT_CUDA(cudaMemcpyAsync(s.host_pmat.data(), s.pmat.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s.st));
+    HOT_CUDA(cudaMemcpyAsync(s.host_pid.data(), s.pid.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s.st));
+  }
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  s.drop_graph();
+  pn_release(s);
+  s.release();
+  s.hd.cl_level = s.hf.cl_level = -1;
+  s.nlev = 0;
+  s.phase = PH_IDLE;
+  s.has_grid = s.has_solution = false;
+  s.parked = true;
+}
+
+void ensure_resident(Scene &s) {
+  if (!s.parked) return;
+  const size_t np = (size_t)s.np;
+  try {
+    upload_tables(s);
+    s.pd.ensure((size_t)PF_COUNT * np + 1, 1.0);
+    s.pmat.ensure(np + 1, 1.0);
+    s.pid.ensure(np + 1, 1.0);
+  } catch (...) {
+    s.release();   // stays parked, nothing half-resident
+    throw;
+  }
+  if (np > 0) {
+    HOT_CUDA(cudaMemcpyAsync(s.pd.p, s.host_pd.data(), sizeof(double) * PF_COUNT * np, cudaMemcpyHostToDevice, s.st));
+    HOT_CUDA(cudaMemcpyAsync(s.pmat.p, s.host_pmat.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s.st));
+    HOT_CUDA(cudaMemcpyAsync(s.pid.p, s.host_pid.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s.st));
+  }
+  HOT_CUDA(cudaStreamSynchronize(s.st));
+  std::vector<double>().swap(s.host_pd);
+  std::vector<int>().swap(s.host_pmat);
+  std::vector<int>().swap(s.host_pid);
+  s.parked = false;
+}
+
+namespace {
+
 void validate_opts(const mpm_solver_opts *o) {
   if (!o) fail(MPM_ERR_INVALID_ARG, "opts is NULL");
   if (!(o->eps > 0.0)) fail(MPM_ERR_INVALID_ARG, "eps must be > 0");
@@ -160,6 +236,14 @@ void validate_opts(const mpm_solver_opts *o) {
   if (o->dt <= 0.0 && !(o->fps > 0.0 && o->cfl > 0.0)) fail(MPM_ERR_INVALID_ARG, "need dt > 0 or fps, cfl > 0");
 }
 
+}  // namespace
+
+// Refresh extension (not in Alg. 3): rebuild the hierarchy at the top of
+// iteration it > 0 every refresh_every iterations.
+bool refresh_due(const mpm_solver_opts &o, int it) { return o.refresh_every > 0 && it > 0 && it % o.refresh_every == 0; }
+
+namespace {
+
 void compute_dt(Scene &s) {
   if (s.opts.dt > 0.0) {
     s.dt = s.opts.dt;
@@ -172,6 +256,7 @@ void compute_dt(Scene &s) {
 }
 
 void do_p2g(Scene &s) {
+  ensure_resident(s);
   s.drop_graph();
   HOT_CUDA(cudaMemsetAsync(s.errflag.p, 0, sizeof(int), s.st));
   compute_dt(s);
@@ -340,7 +425,7 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
       to_newton = true;
       break;
     }
-    if (s.opts.refresh_every > 0 && it > 0 && it % s.opts.refresh_every == 0) {
+    if (refresh_due(s.opts, it)) {
       // extension: the hierarchy at the current iterate, a fresh history
       pn_rebuild_values(s);
       s.hist_n = 0;
@@ -559,25 +644,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc *d, const mpm_solver_opts *o, m
       int dev = 0;
       HOT_CUDA(cudaGetDevice(&dev));
       HOT_CUDA(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev));
-      std::vector<MatParams> mt(d->n_materials);
-      for (int k = 0; k < d->n_materials; ++k) {
-        double E = d->materials[k].E, nu = d->materials[k].nu;
-        mt[k].mu = E / (2.0 * (1.0 + nu));
-        mt[k].lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-        mt[k].xi = std::sqrt(3.0 * (2.0 * mt[k].mu + mt[k].lam) * (2.0 * mt[k].mu + mt[k].lam) +
-                             6.0 * mt[k].lam * mt[k].lam);
-        mt[k].model = d->materials[k].model;
-        mt[k].plastic = d->materials[k].plasticity;
-        mt[k].yield = d->materials[k].yield_stress;
-      }
-      s->mat_table.ensure(mt.size(), 1.0);
-      HOT_CUDA(cudaMemcpyAsync(s->mat_table.p, mt.data(), sizeof(MatParams) * mt.size(), cudaMemcpyHostToDevice, s->st));
-      s->bc_dev.ensure(std::max<size_t>(1, s->bcs.size()), 1.0);
-      if (!s->bcs.empty())
-        HOT_CUDA(cudaMemcpyAsync(s->bc_dev.p, s->bcs.data(), sizeof(mpm_bc) * s->bcs.size(), cudaMemcpyHostToDevice,
-                                 s->st));
-      s->errflag.ensure(4, 1.0);
-      HOT_CUDA(cudaMemsetAsync(s->errflag.p, 0, sizeof(int) * 4, s->st));
+      upload_tables(*s);
       s->pd.ensure((size_t)PF_COUNT * np + 1, 1.0);
       s->pmat.ensure(np + 1, 1.0);
       s->pid.ensure(np + 1, 1.0);
@@ -797,6 +864,7 @@ mpm_status mpm_get_state(mpm_scene_t sc, double *x, double *v, double *F, double
   Scene *s = reinterpret_cast<Scene *>(sc);
   return guarded(s, [&]() -> mpm_status {
     if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    ensure_resident(*s);
     scatter_state_to_user_order(*s, x, v, F, C, to_device != 0);
     return MPM_OK;
   });
@@ -807,6 +875,7 @@ mpm_status mpm_set_state(mpm_scene_t sc, const double *x, const double *v, const
   Scene *s = reinterpret_cast<Scene *>(sc);
   return guarded(s, [&]() -> mpm_status {
     if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    ensure_resident(*s);
     load_state_from_user_order(*s, x, v, F, C, from_device != 0);
     s->phase = PH_IDLE;
     s->has_grid = s->has_solution = false;
@@ -923,6 +992,24 @@ mpm_status mpm_apply_vcycle(mpm_scene_t sc, const double *b, double *u, int32_t 
   });
 }
 
+mpm_status mpm_scene_park(mpm_scene_t sc) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    park_scene(*s);
+    return MPM_OK;
+  });
+}
+
+mpm_status mpm_scene_unpark(mpm_scene_t sc) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  return guarded(s, [&]() -> mpm_status {
+    if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
+    ensure_resident(*s);
+    return MPM_OK;
+  });
+}
+
 mpm_status mpm_set_wait_limit(mpm_scene_t sc, int64_t polls) {
   Scene *s = reinterpret_cast<Scene *>(sc);
   return guarded(s, [&]() -> mpm_status {
@@ -1025,6 +1112,14 @@ mpm_status mpm_scene_footprint(mpm_scene_t sc, int64_t *bytes) {
   Scene *s = reinterpret_cast<Scene *>(sc);
   if (!s || !bytes) return MPM_ERR_INVALID_ARG;
   *bytes = (int64_t)s->bytes();
+  return MPM_OK;
+}
+
+mpm_status mpm_scene_residency(mpm_scene_t sc, int32_t *parked, int64_t *peak_bytes) {
+  Scene *s = reinterpret_cast<Scene *>(sc);
+  if (!s) return MPM_ERR_INVALID_ARG;
+  if (parked) *parked = s->parked ? 1 : 0;
+  if (peak_bytes) *peak_bytes = (int64_t)std::max(s->peak_bytes, s->bytes());
   return MPM_OK;
 }
 

@@ -205,6 +205,13 @@ struct Scene {
   bool loop_graph_ok = true;
   int last_iters = -1;             // L-BFGS iterations of the previous solve
 
+  // parked: every device buffer released, the particle state (sorted SoA,
+  // material ids, original ids) kept in host memory (mpm_scene_park)
+  bool parked = false;
+  std::vector<double> host_pd;
+  std::vector<int> host_pmat, host_pid;
+  size_t peak_bytes = 0;       // largest device footprint seen (admission estimate while parked)
+
   int nlev = 0;
   Topo topo[MAX_LEVELS];
   Hier<double> hd;
@@ -356,5 +363,12 @@ void note_launches(long long n);   // adds to the kernel launch counter
 long long launch_count();
 
 int read_errflag(Scene &s);
+
+// ---- api.cu: refresh rule of the hierarchy-refresh extension
+bool refresh_due(const mpm_solver_opts &o, int it);
+
+// ---- api.cu: residency
+void park_scene(Scene &s);        // device buffers -> host copy of the particle state, buffers released
+void ensure_resident(Scene &s);   // the reverse, when parked
 
 }  // namespace hot

@@ -1,10 +1,24 @@
-// Continuous-batching step server: step requests for resident scenes are
-// queued, admitted as worker slots and memory free up, and run concurrently
-// (each scene on its own CUDA stream, so their kernels overlap on the GPU).
+// Continuous-batching step server with residency admission.
+//
+// Step requests for scenes are queued and admitted as worker slots and device
+// memory free up; admitted requests run concurrently (each scene on its own
+// CUDA stream, so their kernels overlap on the GPU).  The server decides which
+// scenes hold device memory: the device footprint of every scene it manages
+// that is resident (buffers allocated) stays within the budget.  A request
+// whose scene is parked (particle state on the host, no device buffers) needs
+// the scene's largest footprint so far; to make room, idle resident scenes are
+// parked, least recently stepped first.  A request that cannot be given room
+// while other work is in flight waits in the queue; a request that finds
+// nothing in flight is always admitted, so that the queue cannot stall.  Only
+// the particle state survives parking -- the grid, the hierarchy and the
+// L-BFGS history are rebuilt by the next step anyway (Alg. 3 builds them per
+// step).
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
+#include <map>
 #include <mutex>
 #include <set>
 #include <thread>
@@ -20,6 +34,7 @@ struct Request {
   int64_t id;
   Scene *scene;
   Clock::time_point t_submit;
+  bool deferred;   // waited at least once for device memory
 };
 
 struct Finished {
@@ -30,6 +45,24 @@ struct Finished {
   double queue_s;
 };
 
+// What the server knows of a managed scene, updated under its lock only by
+// the thread that owns the scene at that moment (submission, or the worker
+// that stepped or parked it): the scene's own fields change while a worker
+// runs it.
+struct Resid {
+  int64_t bytes = 0;   // device bytes now (0 while parked)
+  int64_t peak = 0;    // largest footprint seen: what it needs when brought back
+  bool parked = false;
+};
+
+Resid snapshot(const Scene *s) {
+  Resid r;
+  r.parked = s->parked;
+  r.bytes = s->parked ? 0 : (int64_t)s->bytes();
+  r.peak = (int64_t)std::max(s->peak_bytes, s->parked ? (size_t)0 : s->bytes());
+  return r;
+}
+
 }  // namespace
 
 struct Server {
@@ -39,53 +72,127 @@ struct Server {
   std::condition_variable cv_work, cv_done;
   std::deque<Request> queue;
   std::deque<Finished> done;
-  std::set<Scene *> busy;
+  std::set<Scene *> busy;        // being stepped or parked by a worker
+  std::list<Scene *> lru;        // scenes the server manages, least recently stepped first
+  std::map<Scene *, Resid> info;
   int64_t in_flight_bytes = 0;
   int64_t peak_in_flight_bytes = 0;
+  int64_t reserved = 0;          // growth admitted for requests in flight (peak of a parked scene, etc.)
+  int64_t peak_resident_bytes = 0;
+  int64_t parks = 0, unparks = 0, deferred = 0;
   int in_flight = 0;
   bool stop = false;
   std::vector<std::thread> workers;
 
-  // first queued request whose scene is idle and whose footprint fits next
-  // to the work already in flight (FIFO otherwise); a lone request is always
-  // admitted so that an over-budget footprint cannot stall the queue
-  bool take(Request &out, int64_t &bytes) {
+  int64_t resident_bytes() const {
+    int64_t r = 0;
+    for (const auto &kv : info) r += kv.second.bytes;
+    return r;
+  }
+
+  // idle resident scenes to park, oldest first, until `need` more bytes fit
+  // next to `resident`; false if they cannot be found
+  bool victims_for(int64_t need, int64_t resident, const Scene *keep, std::vector<Scene *> &out) {
+    out.clear();
+    int64_t r = resident;
+    for (Scene *v : lru) {
+      if (r + need <= budget) break;
+      const Resid &ri = info.at(v);
+      if (v == keep || ri.parked || busy.count(v)) continue;
+      out.push_back(v);
+      r -= ri.bytes;
+    }
+    return r + need <= budget;
+  }
+
+  // first queued request (FIFO) whose scene is idle and for which room can
+  // be made; its victims are returned marked busy
+  bool take(Request &out, int64_t &bytes, int64_t &grow, std::vector<Scene *> &victims) {
+    const int64_t resident = resident_bytes() + reserved;
     for (auto it = queue.begin(); it != queue.end(); ++it) {
-      if (busy.count(it->scene)) continue;
-      int64_t b = (int64_t)it->scene->bytes();
-      if (in_flight > 0 && in_flight_bytes + b > budget) continue;
+      Scene *sc = it->scene;
+      if (busy.count(sc)) continue;
+      const Resid &ri = info.at(sc);
+      // a parked scene needs its peak footprint; a resident one may grow back
+      // to its peak during the step (unknown before its first step)
+      const int64_t need = ri.parked ? ri.peak : std::max<int64_t>(0, ri.peak - ri.bytes);
+      const bool fits = victims_for(need, resident, sc, victims);
+      if (!fits && in_flight > 0) {
+        if (!it->deferred) {
+          it->deferred = true;
+          ++deferred;
+        }
+        continue;
+      }
+      if (!fits) victims_for(need, resident, sc, victims);   // lone request: park what is idle, run anyway
       out = *it;
-      bytes = b;
+      bytes = std::max(ri.peak, ri.bytes);
+      grow = need;
       queue.erase(it);
+      for (Scene *v : victims) {   // counted as parked from now on (the worker parks them first)
+        busy.insert(v);
+        Resid &rv = info[v];
+        rv.bytes = 0;
+        rv.parked = true;
+      }
       return true;
     }
     return false;
+  }
+
+  void touch(Scene *s) {
+    lru.remove(s);
+    lru.push_back(s);
   }
 
   void work() {
     cudaSetDevice(device);
     while (true) {
       Request r;
-      int64_t bytes = 0;
+      int64_t bytes = 0, grow = 0;
+      std::vector<Scene *> victims;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait(lk, [&] { return stop || take(r, bytes); });
+        cv_work.wait(lk, [&] { return stop || take(r, bytes, grow, victims); });
         if (stop) return;
+        reserved += grow;
         busy.insert(r.scene);
         in_flight_bytes += bytes;
         in_flight += 1;
         peak_in_flight_bytes = std::max(peak_in_flight_bytes, in_flight_bytes);
       }
       const auto t_start = Clock::now();
+      for (Scene *v : victims) {
+        try {
+          park_scene(*v);
+        } catch (const Error &) {
+          cudaGetLastError();   // the victim stays resident
+        }
+      }
+      const bool was_parked = r.scene->parked;
       mpm_step_stats st;
       std::memset(&st, 0, sizeof(st));
       mpm_status code = mpm_step(reinterpret_cast<mpm_scene_t>(r.scene), &st);
+      r.scene->peak_bytes = std::max(r.scene->peak_bytes, r.scene->bytes());
       const auto t_end = Clock::now();
+      std::vector<Resid> vsnap;
+      for (Scene *v : victims) vsnap.push_back(snapshot(v));
+      const Resid ssnap = snapshot(r.scene);
       {
         std::lock_guard<std::mutex> lk(mu);
+        for (size_t k = 0; k < victims.size(); ++k) {
+          busy.erase(victims[k]);
+          info[victims[k]] = vsnap[k];
+          if (vsnap[k].parked) ++parks;
+        }
+        info[r.scene] = ssnap;
+        reserved -= grow;
+        if (was_parked && !ssnap.parked) ++unparks;
         busy.erase(r.scene);
+        touch(r.scene);
         in_flight_bytes -= bytes;
         in_flight -= 1;
+        peak_resident_bytes = std::max(peak_resident_bytes, resident_bytes() + reserved);
         done.push_back(Finished{r.id, code, st, std::chrono::duration<double>(t_end - r.t_submit).count(),
                                 std::chrono::duration<double>(t_start - r.t_submit).count()});
       }
@@ -115,10 +222,19 @@ mpm_status mpm_server_submit(mpm_server_t sv, mpm_scene_t scene, int64_t request
   Server *s = reinterpret_cast<Server *>(sv);
   if (!s || !scene) return MPM_ERR_INVALID_ARG;
   hot::Scene *sc = reinterpret_cast<hot::Scene *>(scene);
-  if ((int64_t)sc->bytes() > s->budget) return MPM_ERR_ADMISSION;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    s->queue.push_back(hot::Request{request_id, sc, hot::Clock::now()});
+    auto it = s->info.find(sc);
+    if (it == s->info.end()) {
+      // managed from now on; the caller must not step it concurrently
+      const hot::Resid r = hot::snapshot(sc);
+      if (std::max(r.peak, r.bytes) > s->budget) return MPM_ERR_ADMISSION;
+      s->info[sc] = r;
+      s->lru.push_front(sc);   // never stepped here: first in line to park
+    } else if (std::max(it->second.peak, it->second.bytes) > s->budget) {
+      return MPM_ERR_ADMISSION;
+    }
+    s->queue.push_back(hot::Request{request_id, sc, hot::Clock::now(), false});
   }
   s->cv_work.notify_one();
   return MPM_OK;
@@ -155,6 +271,19 @@ mpm_status mpm_server_info(mpm_server_t sv, int64_t *queued, int64_t *in_flight,
   if (in_flight) *in_flight = s->in_flight;
   if (in_flight_bytes) *in_flight_bytes = s->in_flight_bytes;
   if (peak_in_flight_bytes) *peak_in_flight_bytes = s->peak_in_flight_bytes;
+  return MPM_OK;
+}
+
+mpm_status mpm_server_residency(mpm_server_t sv, int64_t *resident_bytes, int64_t *peak_resident_bytes,
+                                int64_t *parks, int64_t *unparks, int64_t *deferred) {
+  Server *s = reinterpret_cast<Server *>(sv);
+  if (!s) return MPM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (resident_bytes) *resident_bytes = s->resident_bytes();
+  if (peak_resident_bytes) *peak_resident_bytes = s->peak_resident_bytes;
+  if (parks) *parks = s->parks;
+  if (unparks) *unparks = s->unparks;
+  if (deferred) *deferred = s->deferred;
   return MPM_OK;
 }
 

@@ -104,7 +104,7 @@ __global__ void k_ls_after(LoopState *st, int max_ls, double *tr_alpha, int *tr_
 // projected Hessian and its hierarchy are rebuilt at the current iterate and
 // the history restarts, as in the host-driven loop
 __global__ void k_refresh_decide(LoopState *st, int every, cudaGraphConditionalHandle h) {
-  const int go = st->it > 0 && st->it % every == 0;
+  const int go = st->it > 0 && st->it % every == 0;   // the host loop's rule (refresh_due)
   if (go) st->hist_n = 0;
   cudaGraphSetConditional(h, go);
 }
@@ -319,7 +319,8 @@ bool solve_loop_graph(Scene &s, double E0, double norms0[2], double thr, double 
     n_fb2 += f == 2;
   }
   s.graph_launches = (int)(runs + n_fb1);   // V-cycles run inside the graph
-  const long long n_refresh = (refresh > 0 && runs > 1) ? (runs - 1) / refresh : 0;
+  long long n_refresh = 0;   // refreshes taken
+  for (int k = 1; k < runs; ++k) n_refresh += refresh_due(s.opts, k) ? 1 : 0;
   note_launches(c.top + runs * c.body + n_fb1 * c.fb1 + n_fb2 * c.fb2 + (long long)trials_total * c.ls +
                 (long long)it * c.upd + n_refresh * c.refresh);
   return true;

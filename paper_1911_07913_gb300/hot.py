@@ -31,7 +31,8 @@ EXPORTED = ["mpm_set_allocator", "mpm_create_scene", "mpm_destroy_scene", "mpm_l
             "mpm_scene_footprint", "mpm_step_batch", "mpm_profile", "mpm_profile_read",
             "mpm_kernel_launch_count", "mpm_particle_energy_noalloc", "mpm_server_create",
             "mpm_server_submit", "mpm_server_poll", "mpm_server_info", "mpm_server_destroy",
-            "mpm_probe_fp64_fma", "mpm_set_wait_limit"]
+            "mpm_probe_fp64_fma", "mpm_set_wait_limit", "mpm_scene_park", "mpm_scene_unpark",
+            "mpm_scene_residency", "mpm_server_residency"]
 
 
 class mpm_material(C.Structure):
@@ -401,6 +402,18 @@ class HotScene:
             out[nm] = {"ms": float(ms[k]), "launches": int(nl[k])}
         return out
 
+    def park(self):
+        """Particle state to host memory, every device buffer released."""
+        self._check(self.lib.mpm_scene_park(self.h))
+
+    def unpark(self):
+        self._check(self.lib.mpm_scene_unpark(self.h))
+
+    def residency(self) -> dict:
+        p, b = C.c_int32(), C.c_int64()
+        self._check(self.lib.mpm_scene_residency(self.h, C.byref(p), C.byref(b)))
+        return {"parked": bool(p.value), "peak_bytes": b.value}
+
     def footprint(self) -> int:
         b = C.c_int64()
         self._check(self.lib.mpm_scene_footprint(self.h, C.byref(b)))
@@ -465,7 +478,12 @@ class StepServer:
     def info(self) -> dict:
         v = [C.c_int64() for _ in range(4)]
         self.lib.mpm_server_info(self.h, *[C.byref(x) for x in v])
-        return dict(zip(("queued", "in_flight", "in_flight_bytes", "peak_in_flight_bytes"), [x.value for x in v]))
+        out = dict(zip(("queued", "in_flight", "in_flight_bytes", "peak_in_flight_bytes"), [x.value for x in v]))
+        w = [C.c_int64() for _ in range(5)]
+        self.lib.mpm_server_residency(self.h, *[C.byref(x) for x in w])
+        out.update(zip(("resident_bytes", "peak_resident_bytes", "parks", "unparks", "deferred"),
+                       [x.value for x in w]))
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -560,3 +560,76 @@ def test_mixed_step_error_against_fp64_oracle(hot, name):
     assert info["trace"].status == "ok"
     assert rel(og.v + gd["dv"], info["v_new"]) < 1e-3
     assert rel(out["x"], ref.x) < 1e-6
+
+
+def test_park_round_trip_keeps_the_trajectory(hot):
+    """Parking releases every device buffer and keeps the particle state on
+    the host; the next step (which brings the scene back by itself) continues
+    the trajectory as if it had stayed resident."""
+    sc = scenes.batch_scenes(seed=6, count=1, n_min=6000, n_max=6000)[0]
+    opts = scenes.SolverOptions(eps=1e-6, cn_mode=0, levels=3, precision=0, dt=2e-3)
+    ref = hot.HotScene(sc, opts)
+    for _ in range(3):
+        ref.step()
+    a = ref.get_state()
+    ref.close()
+    g = hot.HotScene(sc, opts)
+    g.step()
+    g.park()
+    assert g.residency()["parked"] and g.footprint() == 0 and g.residency()["peak_bytes"] > 0
+    g.step()
+    assert not g.residency()["parked"] and g.footprint() > 0
+    g.park()
+    g.unpark()
+    g.step()
+    b = g.get_state()
+    g.close()
+    assert rel(b["x"], a["x"]) < 1e-12 and rel(b["v"], a["v"]) < 1e-9 and rel(b["F"], a["F"]) < 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_server_admission_binds_and_results_match_alone(hot, precision):
+    """The server keeps the resident footprint of its scenes within a budget
+    of about two scenes: serving five scenes with three workers it parks idle
+    scenes, makes requests wait for memory, and brings parked scenes back;
+    every scene ends where stepping it alone takes it (FP64: x within 1e-12,
+    v within 1e-9; mixed precision, whose FP32 Hessian assembly sums atomics
+    in arrival order: x within 1e-7, v within 1e-3, relative)."""
+    batch = scenes.batch_scenes(seed=5, count=5, n_min=4000, n_max=20000)
+    opts = scenes.SolverOptions(eps=1e-6, cn_mode=0, levels=3, precision=precision, dt=2e-3)
+    steps = [3, 2, 3, 2, 3]
+    alone = []
+    for sc, k in zip(batch, steps):
+        g = hot.HotScene(sc, opts)
+        for _ in range(k):
+            g.step()
+        alone.append(g.get_state())
+        g.close()
+    gs = [hot.HotScene(sc, opts) for sc in batch]
+    for g in gs:              # first step outside the server: each scene's footprint becomes known
+        g.step()
+        g.park()
+    peak = max(g.residency()["peak_bytes"] for g in gs)
+    budget = int(2.2 * peak)
+    srv = hot.StepServer(budget_bytes=budget, n_workers=3)
+    order = [i for r in range(1, 3) for i in range(5) if steps[i] > r]
+    for rid, i in enumerate(order):
+        srv.submit(gs[i], rid)
+    seen = []
+    while True:
+        out = srv.poll(wait=True)
+        if out is None:
+            break
+        assert out["code"] == 0 and out["latency_s"] >= out["queue_s"] >= 0.0
+        seen.append(out["request_id"])
+    info = srv.info()
+    srv.close()
+    assert sorted(seen) == list(range(len(order)))
+    assert info["parks"] >= 1 and info["unparks"] >= 5 and info["deferred"] >= 1, info
+    assert info["peak_resident_bytes"] <= 1.1 * budget, (info, budget)
+    tol_x, tol_v = (1e-12, 1e-9) if precision == 0 else (1e-7, 1e-3)
+    for g, a in zip(gs, alone):
+        b = g.get_state()
+        assert rel(b["x"], a["x"]) < tol_x
+        assert rel(b["v"], a["v"]) < tol_v
+        g.close()
