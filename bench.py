@@ -694,7 +694,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="8k-particle cube (for profiling runs)")
-    ap.add_argument("--workload", default="two_bars_600k", choices=["two_bars_600k", "two_bars_2m", "cube8k"])
+    ap.add_argument("--workload", default="two_bars_600k",
+                    choices=["two_bars_600k", "two_bars_2m", "two_bars_75k", "cube8k"])
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--refresh", type=int, default=REFRESH, help="hierarchy refresh interval (0: Alg. 3 as printed)")
     ap.add_argument("--no-batch", action="store_true")
@@ -729,6 +730,10 @@ def main():
     elif args.workload == "two_bars_2m":
         sc = scenes.two_bars_2m_scene(seed=rank)
         opts = workload_opts(args.precision, args.refresh)
+    elif args.workload == "two_bars_75k":     # small case of the same scene (profiling captures)
+        sc = scenes.two_bars_scene(seed=rank, res=128, width=10, length=47, gap=10)
+        opts = workload_opts(args.precision, args.refresh)
+        opts.levels = 4
     else:
         sc = scenes.two_bars_scene(seed=rank)
         opts = workload_opts(args.precision, args.refresh)

@@ -608,6 +608,54 @@ __global__ void k_residual(int64_t n, const int *__restrict__ row_ptr, const int
   }
 }
 
+// Residual from half of the symmetric matrix (option, flag bit 7): every
+// off-diagonal coupling sits in the earlier-colored prefix of exactly one of
+// its two rows, so the prefixes plus the diagonal blocks hold the matrix
+// once.  r = b - D u first; then each prefix block H_ij of row i gives
+// -H_ij u_j to r_i and, transposed, -H_ij^T u_i to r_j (atomic adds).  Half
+// the matrix bytes of the full residual, three atomics per block.
+template <class T>
+__global__ void k_residual_diag(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ slotpos,
+                                const T *__restrict__ vals, const T *__restrict__ b, const T *__restrict__ u,
+                                T *__restrict__ r) {
+  const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (i >= n) return;
+  const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp, k = slotpos[NSLOT * i + DIAG_SLOT] - rp;
+  const T *v = vals + 9 * (int64_t)rp + k;
+  const T u0 = u[3 * i], u1 = u[3 * i + 1], u2 = u[3 * i + 2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    r[3 * i + c] = b[3 * i + c] - (v[(3 * c) * nb] * u0 + v[(3 * c + 1) * nb] * u1 + v[(3 * c + 2) * nb] * u2);
+}
+
+template <class T>
+__global__ void k_residual_half(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ cols,
+                                const int *__restrict__ nlow, const T *__restrict__ vals, const T *__restrict__ u,
+                                T *r) {
+  const int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+  if (i >= n) return;   // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int rp = row_ptr[i], nb = row_ptr[i + 1] - rp, nl = nlow[i];
+  const T *v = vals + 9 * (int64_t)rp;
+  const T ui0 = u[3 * i], ui1 = u[3 * i + 1], ui2 = u[3 * i + 2];
+  T acc[3] = {T(0), T(0), T(0)};
+  for (int e0 = lane; e0 < nl; e0 += 32) {
+    const int j = cols[rp + e0];
+    T h[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) h[e] = v[e * nb + e0];
+    const T u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
+    acc[0] = fma(h[0], u0, fma(h[1], u1, fma(h[2], u2, acc[0])));
+    acc[1] = fma(h[3], u0, fma(h[4], u1, fma(h[5], u2, acc[1])));
+    acc[2] = fma(h[6], u0, fma(h[7], u1, fma(h[8], u2, acc[2])));
+    atomicAdd(r + 3 * j, -(h[0] * ui0 + h[3] * ui1 + h[6] * ui2));
+    atomicAdd(r + 3 * j + 1, -(h[1] * ui0 + h[4] * ui1 + h[7] * ui2));
+    atomicAdd(r + 3 * j + 2, -(h[2] * ui0 + h[5] * ui1 + h[8] * ui2));
+  }
+  const T sum = warp_sum3_split<T>(acc, lane);
+  if ((lane & 7) == 0 && lane < 24) atomicAdd(r + 3 * i + (lane >> 3), -sum);
+}
+
 // b^{m+1}_J = sum_a R_Ja r_a over the 27 fine nodes a = 2J + o
 template <class T>
 __global__ void k_restrict(int64_t nc, const int *__restrict__ ccoords, const int *__restrict__ fmap, Dims fd,
@@ -1519,7 +1567,15 @@ void vcycle_launches(Scene &s, Hier<T> &h, const double *b_in, double *u_out) {
     Vals<T> &V = h.L[m];
     HOT_CUDA(cudaMemsetAsync(V.u.p, 0, sizeof(T) * 3 * t.n, s.st));
     sgs_symmetric<T>(s, t, V, h, m, true);
-    {
+    if (s.opts.flags & 128) {
+      ProfScope prof_(s, "residual");
+      k_residual_diag<T><<<(unsigned)((t.n + NT - 1) / NT), NT, 0, s.st>>>(t.n, t.row_ptr.p, t.slotpos.p, V.vals.p,
+                                                                          V.b.p, V.u.p, V.r.p);
+      HOT_LAUNCH("k_residual_diag");
+      k_residual_half<T><<<(unsigned)((t.n + WPB - 1) / WPB), NT, 0, s.st>>>(t.n, t.row_ptr.p, t.cols.p, t.nlow.p,
+                                                                           V.vals.p, V.u.p, V.r.p);
+      HOT_LAUNCH("k_residual_half");
+    } else {
       ProfScope prof_(s, "residual");
       k_residual<T><<<(unsigned)((t.n + WPB - 1) / WPB), NT, 0, s.st>>>(
           t.n, t.row_ptr.p, t.cols.p, V.vals.p, V.b.p, V.u.p, V.r.p);

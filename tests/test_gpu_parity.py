@@ -137,12 +137,14 @@ def test_vcycle_matches_oracle_with_same_coarse_count(hot, name):
     assert abs(vc2.cg_counts[0] - its) <= 1
 
 
-@pytest.mark.parametrize("flags", [4, 0, 8, 64])
+@pytest.mark.parametrize("flags", [4, 0, 8, 64, 128])
 def test_vcycle_smoothing_launch_modes(hot, flags):
     """One launch per color (bit 2), one launch per sweep (default: a cluster
     launch on levels whose colors fit a cluster's warps, else cooperative),
-    per-color launches on the finest level only (bit 3) and cooperative
-    launches on every level (bit 6) apply the same V-cycle."""
+    per-color launches on the finest level only (bit 3), cooperative
+    launches on every level (bit 6), and the residual read from half of the
+    symmetric matrix (bit 7, the transposed half by atomics) apply the same
+    V-cycle."""
     sc, opts = SCENES["bars_nh_cn"]
     opts = scenes.SolverOptions(**{**opts.__dict__, "flags": flags})
     g = hot.HotScene(sc, opts)
