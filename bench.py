@@ -266,23 +266,32 @@ def timed_steps(g, steps, stream):
 
 
 def grid_velocity(g):
-    """Node coordinates and v^{n+1} = v^n + dv of the last solved step."""
+    """Node coordinates, v^{n+1} = v^n + dv of the last solved step, node masses."""
     gr = g.grid()
-    return gr["coords"], gr["v"] + gr["dv"]
+    return gr["coords"], gr["v"] + gr["dv"], gr["m"]
 
 
-def mixed_error(c64, v64, x64, c32, v32, x32, x_prev, dx):
+def mixed_error(c64, v64, x64, c32, v32, x32, x_prev, dx, m=None, vp64=None, vp32=None):
     """Error of a mixed-precision step against the FP64 step from the same
-    state: grid v^{n+1} (relative infinity norm over the nodes) and particle
+    state: grid v^{n+1} (relative infinity norm over the nodes, and relative
+    in the mass-weighted norm |M^1/2 v| -- nodes of vanishing mass carry
+    velocities the step barely constrains), particle velocities, and particle
     positions (relative to |x|, in cells, and relative to the step's
     displacement)."""
     if c64.shape != c32.shape or not np.array_equal(c64, c32):
         return {"grid_v_rel": None, "x_rel": None, "note": "node sets differ"}
     dvx = np.abs(x32 - x64).max()
     disp = np.abs(x64 - x_prev).max()
-    return {"grid_v_rel": float(np.abs(v32 - v64).max() / max(np.abs(v64).max(), 1e-300)),
-            "x_rel": float(dvx / np.abs(x64).max()), "x_cells": float(dvx / dx),
-            "x_rel_to_step_displacement": float(dvx / max(disp, 1e-300))}
+    out = {"grid_v_rel": float(np.abs(v32 - v64).max() / max(np.abs(v64).max(), 1e-300)),
+           "x_rel": float(dvx / np.abs(x64).max()), "x_cells": float(dvx / dx),
+           "x_rel_to_step_displacement": float(dvx / max(disp, 1e-300))}
+    if m is not None:
+        w = m[:, None]
+        out["grid_v_rel_mass_weighted"] = float(np.sqrt(np.sum(w * (v32 - v64) ** 2) /
+                                                        max(np.sum(w * v64 ** 2), 1e-300)))
+    if vp64 is not None:
+        out["particle_v_rel"] = float(np.abs(vp32 - vp64).max() / max(np.abs(vp64).max(), 1e-300))
+    return out
 
 
 def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, local, sample_clocks=True, profile_run=False,
@@ -339,13 +348,14 @@ def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, local, sample_clocks=Tr
             s_k = g.get_state() if g2 is not None else None
             prof_stats.append(g.step(check=False))
             if g2 is not None:
-                c64, v64 = grid_velocity(g)
-                x64 = g.get_state()["x"]
+                c64, v64, m64 = grid_velocity(g)
+                s64 = g.get_state()
                 replay_state(g2, sc, s_k)
                 partner_stats.append(g2.step(check=False))
-                c32, v32 = grid_velocity(g2)
-                x32 = g2.get_state()["x"]
-                errors.append(mixed_error(c64, v64, x64, c32, v32, x32, s_k["x"], sc.dx))
+                c32, v32, _ = grid_velocity(g2)
+                s32 = g2.get_state()
+                errors.append(mixed_error(c64, v64, s64["x"], c32, v32, s32["x"], s_k["x"], sc.dx, m=m64,
+                                          vp64=s64["v"], vp32=s32["v"]))
         torch.cuda.synchronize()
         out["prof"] = g.profile_read()
         out["prof_stats"] = prof_stats
@@ -666,7 +676,8 @@ def summarize_pair(r, sc, peaks, traffic_key_mixed, ws=1):
     f, m = out["fp64"]["value"], out["mixed"]["value"]
     out["speedup_mixed_over_fp64"] = (m / f) if f > 0 else None
     errs = p.get("errors") or []
-    keys = ("grid_v_rel", "x_rel", "x_cells", "x_rel_to_step_displacement")
+    keys = ("grid_v_rel", "grid_v_rel_mass_weighted", "particle_v_rel", "x_rel", "x_cells",
+            "x_rel_to_step_displacement")
     out["error_vs_fp64"] = {
         "how": "each step k: the mixed scene steps from the FP64 state S_k; its grid v^{n+1} and particle x are "
                "compared with the FP64 step from S_k",

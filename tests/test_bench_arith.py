@@ -84,6 +84,14 @@ def test_mixed_error_metrics():
     assert e["x_rel_to_step_displacement"] == pytest.approx(2e-6)
     e2 = bench.mixed_error(c, v64, x64, c[::-1].copy(), v32, x32, xp, 0.01)
     assert e2["grid_v_rel"] is None
+    # mass-weighted: a node of vanishing mass barely counts
+    m = np.array([1.0, 1.0, 1e-12, 1.0])
+    v32b = v64.copy()
+    v32b[2] += 1.0
+    e3 = bench.mixed_error(c, v64, x64, c, v32b, x32, xp, 0.01, m=m, vp64=v64[:2], vp32=v64[:2] * 1.5)
+    assert e3["grid_v_rel"] == pytest.approx(1.0)
+    assert e3["grid_v_rel_mass_weighted"] == pytest.approx(np.sqrt(3e-12 / (9.0 + 3e-12)))
+    assert e3["particle_v_rel"] == pytest.approx(0.5)
 
 
 def test_pair_summary_speedup_and_error_maxima():
