@@ -381,8 +381,11 @@ __global__ void __launch_bounds__(HNT) k_hessian_cells(const double *__restrict_
     if (has_pair) {
       const T *Bi = sB + 27 * pi;
       const T dl0 = sd[3 * pl], dl1 = sd[3 * pl + 1], dl2 = sd[3 * pl + 2];
+      // three FMA into the accumulator (a product summed apart, then added,
+      // would cost a fourth FP64 instruction per entry)
 #pragma unroll
-      for (int ab = 0; ab < 9; ++ab) acc[ab] += Bi[3 * ab] * dl0 + Bi[3 * ab + 1] * dl1 + Bi[3 * ab + 2] * dl2;
+      for (int ab = 0; ab < 9; ++ab)
+        acc[ab] = fma(Bi[3 * ab + 2], dl2, fma(Bi[3 * ab + 1], dl1, fma(Bi[3 * ab], dl0, acc[ab])));
     }
   }
   __syncthreads();
