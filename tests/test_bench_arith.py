@@ -110,3 +110,16 @@ def test_pair_summary_speedup_and_error_maxima():
     assert out["speedup_mixed_over_fp64"] == pytest.approx(1.0)
     assert out["error_vs_fp64"]["max"]["grid_v_rel"] == pytest.approx(3e-6)
     assert out["mixed"]["converged_steps"] == 1
+
+
+def test_reference_arm_line(capsys):
+    """bench.py --impl reference: the oracle on the CPU sample, one JSON line
+    with the GPU arm's metric and credit rule (one oracle step, ~10 s)."""
+    import argparse
+    import json
+    bench.run_reference(argparse.Namespace(gpus=1, steps=1, warmup=0))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["converged_steps"] == 1 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
