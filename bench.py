@@ -155,7 +155,7 @@ def barrier(ws: int):
         dist.barrier()
 
 
-def algorithmic_units(name: str, stats_list, n_particles: int, precision: int):
+def algorithmic_units(name: str, stats_list, n_particles: int, precision: int, launches=None):
     """Algorithmic work of kernel `name` summed over the timed steps.
 
     vcycle (the captured V-cycle of Alg. 2): per level m < M-1 four
@@ -166,9 +166,12 @@ def algorithmic_units(name: str, stats_list, n_particles: int, precision: int):
     9 FMA = 18 flop per block visit (the FP64 pipe bounds it).  FP32: 36 B of
     block values + 4 B column index per block visit (HBM bounds it).  The
     coarsest PCG (latency bound, shared-memory resident) is not counted.
-    hessian_cells: 27*27*3 + 378*9*3 FMA = 24,786 flop per particle."""
+    hessian_cells: 27*27*3 + 378*9*3 FMA = 24,786 flop per particle and
+    launch (one launch per hierarchy build: several per step with the
+    refresh; `launches` when known, else one per step)."""
     if name == "hessian_cells":
-        return 2 * (27 * 27 * 3 + 378 * 9 * 3) * n_particles * len(stats_list), "flop"
+        n_launch = launches if launches is not None else len(stats_list)
+        return 2 * (27 * 27 * 3 + 378 * 9 * 3) * n_particles * n_launch, "flop"
     visits = 0
     for st in stats_list:
         nl = st["n_levels"]
@@ -201,12 +204,13 @@ def roofline_entry(name, prof, stats_list, n_particles, precision, peaks, traffi
     p = prof.get(name)
     if not p or p["launches"] == 0:
         return None
-    units, kind = algorithmic_units(name, stats_list, n_particles, precision)
+    units, kind = algorithmic_units(name, stats_list, n_particles, precision, launches=p["launches"])
     secs = p["ms"] / 1e3
     traffic = vcycle_traffic(traffic_key) if (traffic_key and name == "vcycle") else None
-    base = {"kernel": name, "traffic": traffic, "traffic_unit": "DRAM bytes per V-cycle (ncu)", "launches": p["launches"],
+    base = {"kernel": name, "traffic": traffic,
+            "traffic_unit": "DRAM bytes per V-cycle (ncu)" if name == "vcycle" else None, "launches": p["launches"],
             "avg_launch_ms": p["ms"] / p["launches"], "algorithmic_total": units, "algorithmic_unit": kind,
-            "timed": "CUDA events around every V-cycle, over a replay of the timed steps from their start state"}
+            "timed": f"CUDA events around every {name} launch, over a replay of the timed steps from their start state"}
     if kind == "flop":
         achieved = units / secs / 1e12
         out = {**base, "bound": "alu", "achieved": achieved, "peak": round(FP64_PEAK_TFLOPS, 3),
@@ -340,7 +344,7 @@ def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, local, sample_clocks=Tr
         g2.profile(False)
     if not profile_run:
         replay_state(g, sc, start_state)
-        g.profile(True, only=dominant)
+        g.profile(True, only=f"{dominant},hessian_cells")
         if g2 is not None:
             g2.profile(True, only="vcycle")
         prof_stats, errors, partner_stats = [], [], []
@@ -763,6 +767,8 @@ def main():
     prec_key = "fp64" if opts.precision == 0 else "mixed"
     roof = roofline_entry(args.dominant, r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
                           traffic_key=f"{args.workload}_{prec_key}_bytes_per_vcycle", fp64_probe=probe)
+    roof_hess = roofline_entry("hessian_cells", r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
+                               fp64_probe=probe) if opts.precision == 0 else None
     mixed = {}
     if partner is not None and "partner" in r and opts.precision == 0:
         mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_bytes_per_vcycle", ws)
@@ -803,6 +809,7 @@ def main():
             "per_step": rec, "warmup_status": [int(s["status"]) for s in r["warm"]],
             "p50_ms": float(np.percentile(sm, 50)), "p99_ms": float(np.percentile(sm, 99)),
             "e2e": e2e, "gpu_launches": int(r["launches"]), "roofline": roof,
+            "roofline_hessian_assembly": roof_hess,
             "lbfgs_loop_on_device": r["device_loop"],
             "kernel_ms_one_step": {k: round(v["ms"], 3) for k, v in r["breakdown"].items()},
             "clocks": r["clocks"], "fp64_probe_tflops": probe, "mixed": mixed or None,

@@ -274,7 +274,7 @@ mpm_status mpm_get_inner_iters(mpm_scene_t s, int32_t capacity, int32_t *n, int3
 
 /* Per-kernel device timing.  mpm_profile(s, 1, only) clears and starts
  * recording CUDA events on the scene's stream around the library's main
- * kernels (only the kernel named `only` when it is not NULL);
+ * kernels (only the kernels named in `only`, a comma-separated list, when it is not NULL);
  * mpm_profile(s, 0, NULL) stops.  mpm_profile_read returns, per kernel name (32
  * bytes each in `names`), the summed event time in ms and the launch count;
  * *count gets the number of names (entries beyond capacity are dropped). */

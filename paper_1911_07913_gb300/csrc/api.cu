@@ -34,6 +34,20 @@ void note_launch(const char *what) {
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// `only`: empty (every name) or a comma-separated list of names
+bool prof_selected(const std::string &only, const char *name) {
+  if (only.empty()) return true;
+  const std::string n(name);
+  size_t a = 0;
+  while (a <= only.size()) {
+    size_t b = only.find(',', a);
+    if (b == std::string::npos) b = only.size();
+    if (only.compare(a, b - a, n) == 0 && b - a == n.size()) return true;
+    a = b + 1;
+  }
+  return false;
+}
+
 static cudaEvent_t take_event(Scene &s) {
   if (!s.ev_pool.empty()) {
     cudaEvent_t e = s.ev_pool.back();
@@ -50,7 +64,7 @@ ProfScope::ProfScope(Scene &sc, const char *name) : s(&sc), id(-1) {
   // no events inside a stream capture (conditional graph bodies refuse them)
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(sc.st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
-  if (!sc.prof_only.empty() && sc.prof_only != name) return;
+  if (!prof_selected(sc.prof_only, name)) return;
   for (size_t k = 0; k < sc.prof_names.size(); ++k)
     if (sc.prof_names[k] == name) id = (int)k;
   if (id < 0) {

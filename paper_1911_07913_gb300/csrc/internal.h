@@ -238,7 +238,7 @@ struct Scene {
 
   // per-kernel device timing
   bool prof = false;
-  std::string prof_only;                // record only this kernel name when non-empty
+  std::string prof_only;                // record only these kernel names (comma-separated) when non-empty
   std::vector<std::string> prof_names;
   std::vector<int> prof_ids;
   std::vector<cudaEvent_t> prof_ev;     // start/stop pairs, in launch order
@@ -363,6 +363,7 @@ void note_launches(long long n);   // adds to the kernel launch counter
 long long launch_count();
 
 int read_errflag(Scene &s);
+bool prof_selected(const std::string &only, const char *name);   // api.cu: is `name` in the filter
 
 // ---- api.cu: refresh rule of the hierarchy-refresh extension
 bool refresh_due(const mpm_solver_opts &o, int it);

@@ -1626,7 +1626,11 @@ void vcycle(Scene &s, Hier<T> &h, const double *b_in, double *u_out, bool use_gr
   if (s.topo[0].n == 0) return;
   vcycle_prepare<T>(s, h);
   ProfScope prof_(s, "vcycle");
-  if (use_graph && s.graphs_ok && !(s.opts.flags & 1) && (!s.prof || s.prof_only == "vcycle")) {
+  // profiling of kernels inside the V-cycle needs its eager launches
+  const bool inner_prof = s.prof && (s.prof_only.empty() || prof_selected(s.prof_only, "sgs") ||
+                                     prof_selected(s.prof_only, "residual") || prof_selected(s.prof_only, "coarse_pcg") ||
+                                     prof_selected(s.prof_only, "sgs_l0"));
+  if (use_graph && s.graphs_ok && !(s.opts.flags & 1) && !inner_prof) {
     if (s.vgraph && (s.vgraph_b != b_in || s.vgraph_u != u_out)) {
       cudaGraphExecDestroy(s.vgraph);
       s.vgraph = nullptr;

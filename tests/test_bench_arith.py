@@ -123,3 +123,14 @@ def test_reference_arm_line(capsys):
     assert line["converged_steps"] == 1 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_hessian_roofline_counts_every_build():
+    """With the hierarchy refreshed, the fine Hessian is assembled several
+    times per step: its flops are counted per launch, not per step."""
+    st = _stats([1000, 30], [100, 3], vcycles=4)
+    prof = {"hessian_cells": {"ms": 10.0, "launches": 5}}
+    r = bench.roofline_entry("hessian_cells", prof, [st, st], 1000, 0, {})
+    flop = 2 * (27 * 27 * 3 + 378 * 9 * 3) * 1000 * 5
+    assert r["algorithmic_total"] == flop and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(flop / 10e-3 / 1e12)
