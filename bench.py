@@ -420,7 +420,12 @@ def run_batching(seed, steps, count=64):
     opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, precision=1, max_iters=500, refresh_every=REFRESH)
     gs = [hot.HotScene(sc, opts) for sc in scs]
     hot.step_batch(gs, check=False)       # warm-up: allocations, first hierarchy
-    tuned = hot.batch_autotune(gs, 1)     # launch configuration: 6 more (ordinary) steps
+    tuned = hot.batch_autotune(gs, 1)     # launch configuration: more (ordinary) steps
+    f = tuned["flags"]
+    tuned["launch"] = ("V-cycle graph, cooperative sweeps" if not f & 1 else
+                       "eager V-cycle, one launch per color" if f & 4 else "eager V-cycle, cooperative sweeps")
+    if f & 4:
+        tuned["sweep_rows_per_block"] = (8, 2, 4, 16)[(f >> 8) & 3]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     iters, conv = [], 0

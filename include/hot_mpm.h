@@ -130,6 +130,10 @@ typedef struct {
                             colors on levels with at most 64 rows per color);
                             bit 6: cooperative launches on those levels too (bits 2, 3 and 6
                             change launch boundaries only, not the arithmetic);
+                            bit 7: residual from half of the symmetric matrix (prefix blocks and
+                            the transposed half by atomics; measured slower, an option only);
+                            bits 8-9: rows (warps) per block of the one-launch-per-color sweeps:
+                            0 -> 8, 1 -> 2, 2 -> 4, 3 -> 16 (launch shape only);
                             bit 4: drive the L-BFGS iterations from the host;
                             bit 5: run them as one CUDA graph whose conditional nodes take every
                             decision on the device (by default the graph is used once the
@@ -300,12 +304,12 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
  * `steps` real batched steps under each candidate -- the V-cycle as a CUDA
  * graph with one cooperative launch per smoothing sweep (options bits 0 and
  * 2 clear), the V-cycle launched eagerly (bit 0), eagerly with one launch
- * per Gauss-Seidel color (bits 0 and 2) -- with half and all of the host
- * cores as worker threads, then keeps the fastest: the scenes' bits 0 and 2
- * are set to it and mpm_step_batch uses its worker count from then on.  The
- * candidates differ in launch boundaries only, so the tuning steps are
- * ordinary steps of the scenes (steps x 3 x the number of distinct worker
- * counts).  Outputs (may be NULL): the chosen bits, workers, particle-steps/s
+ * per Gauss-Seidel color (bits 0 and 2) with 2, 4, 8 or 16 rows per block
+ * (bits 8-9) -- with half, all and twice the host cores as worker threads,
+ * then keeps the fastest: the scenes' bits 0, 2, 8 and 9 are set to it and
+ * mpm_step_batch uses its worker count from then on.  The candidates differ
+ * in launch shape only, so the tuning steps are ordinary steps of the scenes
+ * (steps x 6 x the number of distinct worker counts).  Outputs (may be NULL): the chosen bits, workers, particle-steps/s
  * and the number of steps each scene took while tuning. */
 mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int32_t *flags_out,
                               int32_t *workers_out, double *rate_out, int32_t *steps_run_out);

@@ -836,15 +836,25 @@ mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int
   }
   const unsigned hc = std::thread::hardware_concurrency();
   const int cores = hc ? (int)hc : 8;
-  std::vector<int> wl = {std::max(1, cores / 2), cores};
-  if (wl[0] == wl[1]) wl.pop_back();
+  std::vector<int> wl = {std::max(1, cores / 2), cores, 2 * cores};
+  if (wl[0] == wl[1]) wl.erase(wl.begin());
+  // candidates: launch mode (bits 0, 2) x rows per block of the per-color
+  // sweeps (bits 8-9, only where those launches run) x worker threads
+  std::vector<int> cand;
+  for (int mode : kTuneModes) {
+    if (mode & 4)
+      for (int wb = 0; wb < 4; ++wb) cand.push_back(mode | (wb << 8));
+    else
+      cand.push_back(mode);
+  }
+  const int kTuned = 5 | (3 << 8);
   double best = -1.0;
   int best_mode = 0, best_w = cores, runs = 0;
-  for (int mode : kTuneModes) {
+  for (int mode : cand) {
     for (int w : wl) {
       for (int i = 0; i < n; ++i) {
         Scene *s = reinterpret_cast<Scene *>(scenes[i]);
-        s->opts.flags = (s->opts.flags & ~5) | mode;
+        s->opts.flags = (s->opts.flags & ~kTuned) | mode;
       }
       g_batch_workers.store(w);
       const auto t0 = std::chrono::steady_clock::now();
@@ -864,7 +874,7 @@ mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int
   }
   for (int i = 0; i < n; ++i) {
     Scene *s = reinterpret_cast<Scene *>(scenes[i]);
-    s->opts.flags = (s->opts.flags & ~5) | best_mode;
+    s->opts.flags = (s->opts.flags & ~kTuned) | best_mode;
   }
   g_batch_workers.store(best_w);
   if (flags_out) *flags_out = best_mode;

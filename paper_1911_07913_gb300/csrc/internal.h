@@ -8,6 +8,11 @@ namespace hot {
 constexpr int MAX_LEVELS = 8;
 constexpr int MAX_HIST = 16;
 constexpr int DEVICE_LOOP_MIN_ITERS = 8;
+// warps (rows) per block of the one-launch-per-color sweeps, from options flag bits 8-9
+inline int sgs_color_warps(int flags) {
+  static const int w[4] = {8, 2, 4, 16};
+  return w[(flags >> 8) & 3];
+}
 constexpr int NSLOT = 125;       // 5^3 block offsets per row (Sec. 6 "Sparse matrix storage")
 constexpr int DIAG_SLOT = 62;    // offset (0,0,0)
 

@@ -543,7 +543,7 @@ template <class T>
 __global__ void k_sgs_color(const int4 *__restrict__ rec, int nrows, const int *__restrict__ cols,
                             const T *__restrict__ vals, const T *__restrict__ dinv, const T *__restrict__ b, T *u,
                             int low) {
-  const int g = blockIdx.x * WPB + (threadIdx.x >> 5);
+  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);   // one warp per row
   if (g >= nrows) return;   // warp-uniform
   const int lane = threadIdx.x & 31;
   const int4 r = rec[g];
@@ -1415,9 +1415,12 @@ void sgs_symmetric(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, int m, bool from_z
     launch_sgs_persistent<T>(s, t, V, h, plan, max_rows);
     return;
   }
+  // rows (warps) per block of the per-color launches: options flag bits 8-9
+  // (0: 8, 1: 2, 2: 4, 3: 16), picked by the batch autotuner
+  const int wpb = sgs_color_warps(s.opts.flags);
   for (int k = 0; k < plan.steps; ++k) {
     ProfScope prof_(s, "sgs");
-    k_sgs_color<T><<<(unsigned)((plan.nr[k] + WPB - 1) / WPB), NT, 0, s.st>>>(
+    k_sgs_color<T><<<(unsigned)((plan.nr[k] + wpb - 1) / wpb), 32 * wpb, 0, s.st>>>(
         t.color_rec.p + plan.off[k], plan.nr[k], t.cols.p, V.vals.p, V.dinv.p, V.b.p, V.u.p,
         k < plan.low_steps ? 1 : 0);
     HOT_LAUNCH("k_sgs_color");

@@ -137,7 +137,7 @@ def test_vcycle_matches_oracle_with_same_coarse_count(hot, name):
     assert abs(vc2.cg_counts[0] - its) <= 1
 
 
-@pytest.mark.parametrize("flags", [4, 0, 8, 64, 128])
+@pytest.mark.parametrize("flags", [4, 0, 8, 64, 128, 4 | (1 << 8), 4 | (3 << 8)])
 def test_vcycle_smoothing_launch_modes(hot, flags):
     """One launch per color (bit 2), one launch per sweep (default: a cluster
     launch on levels whose colors fit a cluster's warps, else cooperative),
@@ -479,7 +479,9 @@ def test_batch_autotune_steps_are_ordinary_steps(hot):
     tuned = [hot.HotScene(sc, opts) for sc in scs]
     plain = [hot.HotScene(sc, opts) for sc in scs]
     choice = hot.batch_autotune(tuned, 1)
-    assert choice["flags"] in (0, 1, 5) and choice["workers"] >= 1 and choice["particle_steps_per_s"] > 0
+    f = choice["flags"]
+    assert (f & 5) in (0, 1, 5) and (f >> 8 == 0 or f & 4) and f & ~(5 | (3 << 8)) == 0
+    assert choice["workers"] >= 1 and choice["particle_steps_per_s"] > 0
     for g in plain:
         for _ in range(choice["steps_run"]):
             g.step()
