@@ -526,6 +526,34 @@ def _serve_phase(srv, gs, scs, rng, count, requests, load, cap_rate=None, rid0=0
     return np.array(lat) * 1e3, wall, sum(scs[i].n for i in pick), bad
 
 
+def run_stiffness_sweep(seed, steps=2, warmup=2, E_mids=(1e5, 1e6, 1e7, 1e8, 1e9, 1e10)):
+    """The varying-stiffness experiment of Sec. 6.4: a bar of three segments
+    twisted by its ends, the end segments at 1e5 Pa, the middle one swept up
+    to 1e10 Pa (38,400 particles, dx = 1/128, FCR, FP64, CN eps 1e-7, 4
+    levels): L-BFGS iterations and device time per step for HOT (with the
+    benchmark's hierarchy refresh) and PN-MGPCG, the same steps for each."""
+    import torch
+    from paper_1911_07913_gb300 import hot
+    out = {"workload": f"three-material bar 10x10x48 cells at dx=1/128, {steps} steps after {warmup} warm-up "
+                       "steps per stiffness, FP64, CN eps 1e-7, 4 levels", "E_mid": list(E_mids)}
+    for name, solver, refresh in (("hot", 0, REFRESH), ("pn_mgpcg", 2, 0)):
+        rows = []
+        for E in E_mids:
+            sc = scenes.three_material_bar_scene(seed=seed, E_mid=E)
+            opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=4, precision=0, max_iters=500, solver=solver,
+                                        refresh_every=refresh)
+            stream = torch.cuda.Stream()
+            g = hot.HotScene(sc, opts, stream=stream.cuda_stream)
+            for _ in range(warmup):
+                g.step(check=False)
+            stats, ms, tot = timed_steps(g, steps, stream)
+            g.close()
+            rec = step_record(stats)
+            rows.append({"iters": rec["iters"], "converged": rec["converged"], "ms_per_step": round(tot / steps, 2)})
+        out[name] = rows
+    return out
+
+
 def run_serving(seed, count=256, requests=512, workers=12, budget_gb=150.0, load=0.8, flags=0,
                 bind_fraction=0.25):
     """Resident scenes behind the continuous-batching server.  For each budget
@@ -788,6 +816,7 @@ def main():
     if args.workload == "two_bars_600k" and args.precision == 0:
         if not args.no_solvers:
             solvers = run_solvers(rank)
+            solvers["stiffness_sweep"] = run_stiffness_sweep(rank)
         if not args.no_batch:
             batching = run_batching(rank, max(2, args.steps // 2))
         if not args.no_serve:

@@ -220,6 +220,37 @@ def two_bars_scene(seed: int = 0, res: int = 256, width: int = 20, length: int =
                      f"two_bars_w{width}_l{length}_r{res}")
 
 
+def three_material_bar_scene(seed: int = 0, res: int = 128, width: int = 10, length: int = 48,
+                             E_ends: float = 1e5, E_mid: float = 1e8, nu: float = 0.4, rho: float = 2000.0,
+                             model: int = MODEL_FCR, omega: float = 1.0, end_cells: int = 3,
+                             gravity=(0.0, -9.8, 0.0)) -> Scene:
+    """A bar along z in three equal segments, twisted by its ends (the
+    varying-stiffness experiment of Sec. 6.4): the two end segments keep
+    E_ends, the middle one takes E_mid (the paper sweeps it from 1e5 to 1e10
+    Pa).  FCR as in all of the paper's examples; the end layers are held in
+    cylinders about the bar axis and rotate at +omega / -omega."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / res
+    origin = np.zeros(3)
+    c = res // 2
+    x0, y0, z0 = c - width // 2, c - width // 2, c - length // 2
+    x1, y1, z1 = x0 + width, y0 + width, z0 + length
+    xb = _jittered_block(rng, (x0, y0, z0), (x1, y1, z1), dx, origin)
+    seg = (xb[:, 2] / dx - z0) * 3.0 / length
+    mat = np.where((seg >= 1.0) & (seg < 2.0), 1, 0).astype(np.int32)
+    mats = [Material(E_ends, nu, rho, model), Material(E_mid, nu, rho, model)]
+    center = (0.5 * (x0 + x1) * dx, 0.5 * (y0 + y1) * dx, 0.0)
+    radius = (np.sqrt(0.5) * width + 2.0) * dx
+    lo_x, hi_x = center[0] - radius, center[0] + radius
+    lo_y, hi_y = center[1] - radius, center[1] + radius
+    bcs = [BoundaryBox(BC_ROTATE, (lo_x, lo_y, (z0 - 3) * dx), (hi_x, hi_y, (z0 + end_cells + 0.5) * dx),
+                       (0.0, 0.0, 1.0), center, omega, radius),
+           BoundaryBox(BC_ROTATE, (lo_x, lo_y, (z1 - end_cells - 0.5) * dx), (hi_x, hi_y, (z1 + 3) * dx),
+                       (0.0, 0.0, 1.0), center, -omega, radius)]
+    return _assemble(xb, np.zeros_like(xb), mat, mats, dx, 8, origin, (res, res, res), gravity, bcs,
+                     f"three_material_bar_w{width}_l{length}_r{res}_Emid{E_mid:g}")
+
+
 def two_bars_2m_scene(seed: int = 0) -> Scene:
     """The two-bar scene at 1.5x resolution: dx = 1/384, bars 30 x 30 x 141
     cells, 8 particles per cell (2,030,400 particles)."""
