@@ -31,6 +31,9 @@ def make_scenes():
         "cube8k_fcr": (scenes.cube_scene(seed=0), scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=2e-3, levels=3)),
         "bars_nh_cn": (bars, scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3)),
         "bars_cyl": (bars_cyl, scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3)),
+        # the stretched box of Sec. 6.3 (diag F^n ~ U[0.7, 1.3], no gravity, no boundary conditions)
+        "stretched_box": (scenes.stretched_box_scene(seed=2), scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3,
+                                                                                  dt=1.0 / 24)),
         # the varying-stiffness experiment of Sec. 6.4: middle segment 1e4 x stiffer than the ends
         "tribar_1e9": (scenes.three_material_bar_scene(seed=6, res=64, width=6, length=18, E_mid=1e9),
                        scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3)),
