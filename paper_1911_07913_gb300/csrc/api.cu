@@ -387,7 +387,10 @@ void pn_loop(Scene &s, double &E, double norms[2], double thr, double &nrm, int 
 
 mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   if (s.phase < PH_P2G) fail(MPM_ERR_STATE, "mpm_p2g must run before mpm_solve_step");
-  if (s.phase < PH_HIER) do_build(s);
+  // The projected Hessian and its hierarchy serve the iterations only: they
+  // are built once the termination test at dv = 0 has asked for a first
+  // iteration (a scene at rest under the tolerance skips the build).
+  const bool had_hier = s.phase >= PH_HIER;
   const int64_t n = s.nn(), n3 = 3 * n;
   const int w = s.opts.lbfgs_m;
   for (auto *b : {&s.dv, &s.g, &s.pdir, &s.q, &s.g_new, &s.dv_new, &s.vtmp}) b->ensure(n3 + 3);
@@ -412,10 +415,20 @@ mpm_status do_solve(Scene &s, mpm_step_stats *st) {
   int it = 0, trials_total = 0, cg_total = 0, inner_total = 0;
   double nrm = 0.0;
   const double thr = s.opts.cn_mode == 0 ? s.opts.eps * std::sqrt((double)nfree) : s.opts.eps * g1n;
+  const bool finite0 = std::isfinite(norms[0]) && std::isfinite(norms[1]) && std::isfinite(E);
+  const double nrm0 = std::sqrt(s.opts.cn_mode == 0 ? norms[1] : norms[0]);
+  const bool need_iter = finite0 && !(nrm0 <= thr);
+  if (need_iter && !had_hier) do_build(s);
   if (s.opts.solver != 0) {
-    pn_loop(s, E, norms, thr, nrm, it, trials_total, inner_total, status);
+    if (need_iter) {
+      pn_loop(s, E, norms, thr, nrm, it, trials_total, inner_total, status);
+    } else {
+      nrm = nrm0;
+      if (!finite0) status = MPM_ERR_NUMERIC;
+    }
   }
-  const bool on_device = s.opts.solver == 0 && solve_loop_graph(s, E, norms, thr, E, nrm, it, trials_total, status);
+  const bool on_device =
+      s.opts.solver == 0 && need_iter && solve_loop_graph(s, E, norms, thr, E, nrm, it, trials_total, status);
   bool to_newton = false;   // fallback_after reached (extension)
   while (s.opts.solver == 0 && !on_device) {
     if (!std::isfinite(norms[0]) || !std::isfinite(norms[1]) || !std::isfinite(E)) {
@@ -978,7 +991,8 @@ mpm_status mpm_get_hessian(mpm_scene_t sc, int32_t level, int64_t *n_rows, int64
   Scene *s = reinterpret_cast<Scene *>(sc);
   return guarded(s, [&]() -> mpm_status {
     if (!s) fail(MPM_ERR_INVALID_ARG, "scene is NULL");
-    if (s->phase < PH_HIER) fail(MPM_ERR_STATE, "no hierarchy: call mpm_build_hierarchy or mpm_solve_step");
+    if (s->phase < PH_HIER || s->nlev == 0)
+      fail(MPM_ERR_STATE, "no hierarchy: call mpm_build_hierarchy (or mpm_solve_step on a scene that iterates)");
     if (level < 0 || level >= s->nlev) fail(MPM_ERR_INVALID_ARG, "level out of range");
     Topo &t = s->topo[level];
     if (n_rows) *n_rows = t.n;
@@ -999,7 +1013,7 @@ mpm_status mpm_apply_vcycle(mpm_scene_t sc, const double *b, double *u, int32_t 
   Scene *s = reinterpret_cast<Scene *>(sc);
   return guarded(s, [&]() -> mpm_status {
     if (!s || !b || !u) fail(MPM_ERR_INVALID_ARG, "NULL argument");
-    if (s->phase < PH_HIER) fail(MPM_ERR_STATE, "no hierarchy: call mpm_build_hierarchy first");
+    if (s->phase < PH_HIER || s->nlev == 0) fail(MPM_ERR_STATE, "no hierarchy: call mpm_build_hierarchy first");
     const int64_t n3 = 3 * s->nn();
     s->dv_e.ensure(n3 + 3);
     s->g_e.ensure(n3 + 3);
