@@ -54,10 +54,15 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # dv = 0 alone, L-BFGS stalls on steps whose Hessian changes strongly within
 # the step (measured on these scenes; the comparison is in the design notes).
 REFRESH = 5
+# Multigrid levels of the 2M-particle scene: one more than the 600k scene's 5,
+# so that the coarsest level has the same 105 nodes in both (measured: mixed
+# V-cycle 3.50 -> 2.63 ms, the coarsest CG's ~80 iterations per V-cycle on
+# 312 nodes gone; FP64 step time unchanged, mixed step 4% faster).
+LEVELS_2M = 6
 
 
-def workload_opts(precision: int, refresh: int = REFRESH) -> scenes.SolverOptions:
-    return scenes.SolverOptions(eps=1e-7, cn_mode=0, lbfgs_m=8, levels=5, precision=precision,
+def workload_opts(precision: int, refresh: int = REFRESH, levels: int = 5) -> scenes.SolverOptions:
+    return scenes.SolverOptions(eps=1e-7, cn_mode=0, lbfgs_m=8, levels=levels, precision=precision,
                                 max_iters=500, refresh_every=refresh)
 
 
@@ -746,6 +751,9 @@ def main():
                     choices=["two_bars_600k", "two_bars_2m", "two_bars_75k", "cube8k"])
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--refresh", type=int, default=REFRESH, help="hierarchy refresh interval (0: Alg. 3 as printed)")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="multigrid levels (0: the workload's own, 5 at 600k particles, 6 at 2M)")
+    ap.add_argument("--levels-2m", type=int, default=LEVELS_2M, help="multigrid levels of the 2M pair run after the headline")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-solvers", action="store_true", help="skip the HOT / PN-PCG / PN-MGPCG comparison")
@@ -777,19 +785,19 @@ def main():
         opts = scenes.SolverOptions(eps=1e-6, cn_mode=1, dt=2e-3, levels=3, precision=args.precision)
     elif args.workload == "two_bars_2m":
         sc = scenes.two_bars_2m_scene(seed=rank)
-        opts = workload_opts(args.precision, args.refresh)
+        opts = workload_opts(args.precision, args.refresh, args.levels or LEVELS_2M)
     elif args.workload == "two_bars_75k":     # small case of the same scene (profiling captures)
         sc = scenes.two_bars_scene(seed=rank, res=128, width=10, length=47, gap=10)
         opts = workload_opts(args.precision, args.refresh)
         opts.levels = 4
     else:
         sc = scenes.two_bars_scene(seed=rank)
-        opts = workload_opts(args.precision, args.refresh)
+        opts = workload_opts(args.precision, args.refresh, args.levels or 5)
     peaks = load_peaks()
     probe = None if args.profile_run else hot.probe_fp64_tflops()
     partner = None
     if not args.no_mixed and args.workload != "cube8k":
-        partner = workload_opts(1 - args.precision, args.refresh)
+        partner = workload_opts(1 - args.precision, args.refresh, opts.levels)
     barrier(ws)
     r = run_gpu(sc, opts, args.steps, args.warmup, args.dominant, not args.no_e2e, local,
                 sample_clocks=not args.profile_run, profile_run=args.profile_run, partner_opts=partner,
@@ -807,8 +815,8 @@ def main():
         mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_bytes_per_vcycle", ws)
     if partner is not None and not args.no_2m and args.workload == "two_bars_600k" and opts.precision == 0:
         sc2 = scenes.two_bars_2m_scene(seed=rank)
-        r2 = run_gpu(sc2, workload_opts(0, args.refresh), args.steps, args.warmup, "vcycle", False, local,
-                     partner_opts=workload_opts(1, args.refresh), fp64_probe=probe)
+        r2 = run_gpu(sc2, workload_opts(0, args.refresh, args.levels_2m), args.steps, args.warmup, "vcycle", False,
+                     local, partner_opts=workload_opts(1, args.refresh, args.levels_2m), fp64_probe=probe)
         mixed["two_bars_2m"] = summarize_pair(r2, sc2, peaks, "two_bars_2m_mixed_bytes_per_vcycle", ws)
         mixed["two_bars_2m"]["roofline_fp64_vcycle"] = roofline_entry(
             "vcycle", r2["prof"], r2["prof_stats"], sc2.n, 0, peaks, fp64_probe=probe)

@@ -127,13 +127,17 @@ typedef struct {
                             bit 3: one launch per color on the finest level only (by default
                             each symmetric sweep of each level is one cooperative launch, or
                             one 16-CTA cluster launch with hardware cluster barriers between
-                            colors on levels with at most 64 rows per color);
+                            colors on levels with at most 144 (FP64) or 192 (FP32) rows per
+                            color whose u fits in shared memory, 64 otherwise);
                             bit 6: cooperative launches on those levels too (bits 2, 3 and 6
                             change launch boundaries only, not the arithmetic);
                             bit 7: residual from half of the symmetric matrix (prefix blocks and
                             the transposed half by atomics; measured slower, an option only);
                             bits 8-9: rows (warps) per block of the one-launch-per-color sweeps:
                             0 -> 8, 1 -> 2, 2 -> 4, 3 -> 16 (launch shape only);
+                            bit 10: cluster-launched sweeps read and write u in global memory
+                            (by default each CTA of the cluster holds the level's u in shared
+                            memory and writes new values into every CTA's copy; same results);
                             bit 4: drive the L-BFGS iterations from the host;
                             bit 5: run them as one CUDA graph whose conditional nodes take every
                             decision on the device (by default the graph is used once the
@@ -293,10 +297,12 @@ int64_t mpm_kernel_launch_count(void);
 mpm_status mpm_scene_footprint(mpm_scene_t s, int64_t *bytes);
 
 /* Batched stepping: p2g, solve and g2p of n independent scenes, taken from
- * a shared queue by one worker thread per host core (at most n).  Scenes on
+ * a shared queue by one worker thread per host core (at most n), the scenes
+ * whose previous step in this call took longest first.  Scenes on
  * different streams overlap on the GPU; scenes that share a stream are
- * serialised by it.  stats may be NULL, else n entries.  Returns the first
- * failing scene's status (mpm_last_error(NULL) names the scene). */
+ * serialised by it.  stats may be NULL, else n entries (in the order of
+ * `scenes`).  Returns the first failing scene's status (mpm_last_error(NULL)
+ * names the scene). */
 mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats);
 
 /* Launch-configuration autotuner for batched stepping (configuration 4 of the

@@ -805,6 +805,14 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
   }
   std::vector<mpm_status> res(n, MPM_OK);
   const int workers = batch_workers(n);
+  // longest previous step first: a long step that starts last would set the
+  // batch's end (scenes not yet stepped keep their order)
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const Scene *sa = reinterpret_cast<const Scene *>(scenes[a]), *sb = reinterpret_cast<const Scene *>(scenes[b]);
+    return (sa ? sa->last_step_s : 0.0) > (sb ? sb->last_step_s : 0.0);
+  });
   std::atomic<int> next{0};
   std::vector<std::thread> th;
   th.reserve(workers);
@@ -813,8 +821,13 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
   for (int k = 0; k < workers; ++k)
     th.emplace_back([&]() {
       cudaSetDevice(dev);
-      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1))
+      for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) {
+        const int i = order[q];
+        const auto t0 = std::chrono::steady_clock::now();
         res[i] = mpm_step(scenes[i], stats ? &stats[i] : nullptr);
+        if (Scene *si = reinterpret_cast<Scene *>(scenes[i]))
+          si->last_step_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      }
     });
   for (auto &t : th) t.join();
   for (int i = 0; i < n; ++i)

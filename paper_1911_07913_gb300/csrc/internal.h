@@ -209,6 +209,7 @@ struct Scene {
   cudaStream_t aux_st[2] = {nullptr, nullptr};   // streams for captures of conditional bodies
   bool loop_graph_ok = true;
   int last_iters = -1;             // L-BFGS iterations of the previous solve
+  double last_step_s = 0.0;        // host time of the scene's last step in mpm_step_batch
 
   // parked: every device buffer released, the particle state (sorted SoA,
   // material ids, original ids) kept in host memory (mpm_scene_park)

@@ -487,9 +487,10 @@ __device__ __forceinline__ T ld_u(const T *p) {
   return *p;
 }
 
-template <class T, bool LDCG = true>
-__device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int rp, int nb, int nuse, int lane,
-                                           const int *__restrict__ cols, const T *__restrict__ vals, T *u) {
+// the new u_i of a row held in registers, on lanes 0-2 (component `lane`)
+template <class T, bool LDCG>
+__device__ __forceinline__ T row_new_u(const RowRegs<T> &R, int64_t i, int rp, int nb, int nuse, int lane,
+                                       const int *__restrict__ cols, const T *__restrict__ vals, const T *u) {
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int q = 0; q < SW_PRE; ++q) {
@@ -531,7 +532,14 @@ __device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int r
   const T y = ((lane & 7) == 0 && lane < 24) ? R.bv - sum : T(0);
   const T y0 = __shfl_sync(0xffffffffu, y, 0), y1 = __shfl_sync(0xffffffffu, y, 8),
           y2 = __shfl_sync(0xffffffffu, y, 16);
-  if (lane < 3) u[3 * i + lane] = fma(R.d[2], y2, fma(R.d[1], y1, R.d[0] * y0));
+  return fma(R.d[2], y2, fma(R.d[1], y1, R.d[0] * y0));
+}
+
+template <class T, bool LDCG = true>
+__device__ __forceinline__ void update_row(const RowRegs<T> &R, int64_t i, int rp, int nb, int nuse, int lane,
+                                           const int *__restrict__ cols, const T *__restrict__ vals, T *u) {
+  const T val = row_new_u<T, LDCG>(R, i, rp, nb, nuse, lane, cols, vals, u);
+  if (lane < 3) u[3 * i + lane] = val;
 }
 
 // One row of a Gauss-Seidel color: u_i <- D_i^{-1} (b_i - sum_{j != i} H_ij u_j)
@@ -866,6 +874,67 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_persistent(SweepPlan plan, con
     __syncthreads();
     if (!s_ok) return;
   }
+}
+
+// A whole symmetric sweep of a small level on one thread-block cluster with
+// the level's u held in shared memory: every CTA keeps a copy of all of u,
+// gathers the neighbours' u_j from its own copy, and writes each new u_i into
+// every CTA's copy (distributed shared memory).  The hardware cluster barrier
+// between colors (arrive with release, wait with acquire, at cluster scope)
+// orders those writes; u goes back to global memory once, after the last
+// color.  A color then costs the barrier and on-chip latencies instead of two
+// round trips through L2.  Rows, color order and per-row arithmetic are those
+// of k_sgs_persistent, so the result is bitwise the same.
+template <class T>
+__global__ void __launch_bounds__(SW_NT, 1) k_sgs_cluster_smem(SweepPlan plan, const int4 *__restrict__ rec,
+                                                               const int *__restrict__ cols,
+                                                               const T *__restrict__ vals,
+                                                               const T *__restrict__ dinv, const T *__restrict__ b,
+                                                               T *u, int n) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ int4 s_rec[54][SW_WARPS];
+  extern __shared__ __align__(16) unsigned char sw_dyn[];
+  T *su = reinterpret_cast<T *>(sw_dyn);
+  const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (int)cluster.block_rank();
+  const int first = blockIdx.x + G * warp;
+  for (int k = lane; k < plan.steps; k += 32) {
+    int4 rr = first < plan.nr[k] ? rec[plan.off[k] + first] : make_int4(-1, 0, 0, 0);
+    if (k >= plan.low_steps) rr.w = rr.z;
+    s_rec[k][warp] = rr;
+  }
+  for (int k = threadIdx.x; k < 3 * n; k += SW_NT) su[k] = u[k];
+  // every copy is loaded (and every CTA is running) before any remote write
+  cluster.sync();
+  RowRegs<T> R;
+  {
+    const int4 r0 = s_rec[0][warp];
+    if (r0.x >= 0) load_row<T>(R, r0.x, r0.y, r0.z, r0.w, lane, cols, vals, dinv, b);
+  }
+  for (int k = 0; k < plan.steps; ++k) {
+    const int4 r = s_rec[k][warp];
+    if (r.x >= 0) {   // warp-uniform
+      const T val = row_new_u<T, false>(R, r.x, r.y, r.z, r.w, lane, cols, vals, su);
+      const T w0 = __shfl_sync(0xffffffffu, val, 0), w1 = __shfl_sync(0xffffffffu, val, 1),
+              w2 = __shfl_sync(0xffffffffu, val, 2);
+      if (lane < G) {
+        T *dst = cluster.map_shared_rank(su, lane) + 3 * (int64_t)r.x;
+        dst[0] = w0;
+        dst[1] = w1;
+        dst[2] = w2;
+      }
+    }
+    if (k + 1 == plan.steps) break;
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    const int4 rn = s_rec[k + 1][warp];
+    if (rn.x >= 0) load_row<T>(R, rn.x, rn.y, rn.z, rn.w, lane, cols, vals, dinv, b);
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
+  // every copy is final; no CTA writes another's shared memory after this
+  cluster.sync();
+  for (int k = rank * SW_NT + threadIdx.x; k < 3 * n; k += G * SW_NT) u[k] = su[k];
 }
 
 template <class T>
@@ -1288,12 +1357,15 @@ int persistent_blocks() {
 
 // CTAs of the cluster that runs the sweeps of small levels: 16 where a
 // non-portable cluster of that size can be resident, else 8 (0: none).
-// Measured on the two-bar scenes: with u in global memory, a color behind the
-// cluster barrier costs ~10-16% less than behind the grid barrier when it has
-// a few dozen rows, and more once a color's FP64 rows outgrow 16 SMs (about a
-// hundred rows), hence the row limit.
+// Row limits (largest color of the level), measured per level on the two-bar
+// scenes against the grid-barrier sweep: with u in global memory the cluster
+// sweep wins up to a few dozen FP64 rows per color; with u in shared memory
+// (10-25% faster than in global memory on those levels) FP64 levels win up
+// to ~150 rows per color (135: 11% faster; 234: 57% slower, the FP64 pipe of
+// 16 SMs), FP32 levels up to ~200 (135: 11% faster; 234: 6% slower).
 constexpr int CLUSTER_SWEEP_ROWS = 64;
-constexpr int CLUSTER_SWEEP_ROWS_FP32 = 256;   // FP32 rows do not load the FP64 pipe
+constexpr int CLUSTER_SWEEP_ROWS_SMEM = 144;   // FP64, u in shared memory
+constexpr int CLUSTER_SWEEP_ROWS_FP32 = 192;
 template <class T>
 int sweep_cluster_size() {
   static std::atomic<int> cached{-1};
@@ -1326,12 +1398,59 @@ int sweep_cluster_size() {
   return c;
 }
 
+// Largest level vector (bytes of shared memory) that k_sgs_cluster_smem can
+// hold with a cluster of sweep_cluster_size<T>() CTAs resident; 0: none.
+template <class T>
+size_t sweep_smem_limit() {
+  static std::atomic<long long> cached{-1};
+  long long c = cached.load();
+  if (c < 0) {
+    c = 0;
+    const int cl = sweep_cluster_size<T>();
+    if (cl > 0) {
+      if (cudaFuncSetAttribute(k_sgs_cluster_smem<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess)
+        cudaGetLastError();
+      for (int kb : {192, 160, 128, 96, 64, 48}) {
+        const int bytes = kb * 1024;
+        if (cudaFuncSetAttribute(k_sgs_cluster_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cl);
+        cfg.blockDim = dim3(SW_NT);
+        cfg.dynamicSmemBytes = bytes;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k_sgs_cluster_smem<T>, &cfg) == cudaSuccess && nc >= 1) {
+          c = bytes;
+          break;
+        }
+        cudaGetLastError();
+      }
+    }
+    cached.store(c);
+  }
+  return (size_t)c;
+}
+
 template <class T>
 void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const SweepPlan &plan, int max_rows) {
-  // levels whose colors have at most CLUSTER_SWEEP_ROWS rows: one cluster,
+  // levels whose colors have few rows (the limits above): one cluster,
   // hardware cluster barriers between colors (flag bit 6 turns this off)
   const int CLR = sweep_cluster_size<T>();
-  const int row_limit = sizeof(T) == 4 ? CLUSTER_SWEEP_ROWS_FP32 : CLUSTER_SWEEP_ROWS;
+  // the level's u in shared memory unless it does not fit (or flag bit 10)
+  const size_t smem = 3 * (size_t)t.n * sizeof(T);
+  const bool in_smem = !(s.opts.flags & 1024) && smem <= sweep_smem_limit<T>();
+  const int row_limit = sizeof(T) == 4 ? CLUSTER_SWEEP_ROWS_FP32 : in_smem ? CLUSTER_SWEEP_ROWS_SMEM : CLUSTER_SWEEP_ROWS;
   if (CLR > 0 && !(s.opts.flags & 64) && max_rows <= std::min(row_limit, CLR * SW_WARPS)) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CLR);
@@ -1344,6 +1463,14 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (in_smem) {
+      cfg.dynamicSmemBytes = smem;
+      HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_cluster_smem<T>, plan, (const int4 *)t.color_rec.p,
+                                  (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
+                                  V.u.p, (int)t.n));
+      note_launch("k_sgs_cluster_smem");
+      return;
+    }
     HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T, false, true>, plan, (const int4 *)t.color_rec.p,
                                 (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
                                 V.u.p, (unsigned *)nullptr, s.errflag.p, s.spin_limit));
@@ -1615,8 +1742,9 @@ void vcycle_prepare(Scene &s, Hier<T> &h) {
   h.bar.ensure(4);
   h.cg_log.ensure(4097, 1.0);
   h.part.ensure(2 * (size_t)coop_blocks<T>() + 2);
-  persistent_blocks<T>();   // occupancy queries before any capture
+  persistent_blocks<T>();   // occupancy queries and function attributes before any capture
   sweep_cluster_size<T>();
+  sweep_smem_limit<T>();
   if (h.cl_level != s.nlev - 1) plan_cluster<T>(s, h, s.nlev - 1);
 }
 
