@@ -807,17 +807,17 @@ def main():
     value = credited_rate(sc.n, r["stats"], t_max, ws)
     prec_key = "fp64" if opts.precision == 0 else "mixed"
     roof = roofline_entry(args.dominant, r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
-                          traffic_key=f"{args.workload}_{prec_key}_bytes_per_vcycle", fp64_probe=probe)
+                          traffic_key=f"{args.workload}_{prec_key}_l{opts.levels}_bytes_per_vcycle", fp64_probe=probe)
     roof_hess = roofline_entry("hessian_cells", r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
                                fp64_probe=probe) if opts.precision == 0 else None
     mixed = {}
     if partner is not None and "partner" in r and opts.precision == 0:
-        mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_bytes_per_vcycle", ws)
+        mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_l{opts.levels}_bytes_per_vcycle", ws)
     if partner is not None and not args.no_2m and args.workload == "two_bars_600k" and opts.precision == 0:
         sc2 = scenes.two_bars_2m_scene(seed=rank)
         r2 = run_gpu(sc2, workload_opts(0, args.refresh, args.levels_2m), args.steps, args.warmup, "vcycle", False,
                      local, partner_opts=workload_opts(1, args.refresh, args.levels_2m), fp64_probe=probe)
-        mixed["two_bars_2m"] = summarize_pair(r2, sc2, peaks, "two_bars_2m_mixed_bytes_per_vcycle", ws)
+        mixed["two_bars_2m"] = summarize_pair(r2, sc2, peaks, f"two_bars_2m_mixed_l{args.levels_2m}_bytes_per_vcycle", ws)
         mixed["two_bars_2m"]["roofline_fp64_vcycle"] = roofline_entry(
             "vcycle", r2["prof"], r2["prof_stats"], sc2.n, 0, peaks, fp64_probe=probe)
     batching = serving = solvers = None
