@@ -188,20 +188,33 @@ def algorithmic_units(name: str, stats_list, n_particles: int, precision: int, l
     return 40 * visits, "byte"
 
 
-def vcycle_traffic(key):
-    """DRAM bytes per V-cycle (dram__bytes_read.sum + dram__bytes_write.sum
-    over the kernels of one V-cycle) from the committed ncu summary, or None
-    when the V-cycle's source changed after that capture."""
+# committed ncu DRAM figures per roofline unit: summary file and the source file whose hash pins them
+TRAFFIC_FILES = {"vcycle": ("vcycle_dram.txt", "multigrid.cu"),
+                 "hessian_cells": ("hessian_cells_dram.txt", "elastic.cu")}
+
+
+def kernel_traffic(name, key):
+    """DRAM bytes per roofline unit (dram__bytes_read.sum + dram__bytes_write.sum:
+    over the kernels of one V-cycle, or of one Hessian-assembly launch) from
+    the committed ncu summary, or None when the kernel's source changed after
+    that capture."""
+    if name not in TRAFFIC_FILES:
+        return None
+    summary, source = TRAFFIC_FILES[name]
     try:
-        lines = open(os.path.join(ROOT, "profiles", "vcycle_dram.txt")).read().splitlines()
-        src = open(os.path.join(ROOT, "paper_1911_07913_gb300", "csrc", "multigrid.cu"), "rb").read()
+        lines = open(os.path.join(ROOT, "profiles", summary)).read().splitlines()
+        src = open(os.path.join(ROOT, "paper_1911_07913_gb300", "csrc", source), "rb").read()
     except OSError:
         return None
     kv = dict(line.split(": ", 1) for line in lines if ": " in line and not line.startswith("#"))
-    if kv.get("multigrid_cu_sha256") != hashlib.sha256(src).hexdigest():
+    if kv.get(source.replace(".", "_") + "_sha256") != hashlib.sha256(src).hexdigest():
         return None
     v = kv.get(key)
     return float(v) if v else None
+
+
+def vcycle_traffic(key):
+    return kernel_traffic("vcycle", key)
 
 
 def roofline_entry(name, prof, stats_list, n_particles, precision, peaks, traffic_key=None, fp64_probe=None):
@@ -211,9 +224,10 @@ def roofline_entry(name, prof, stats_list, n_particles, precision, peaks, traffi
         return None
     units, kind = algorithmic_units(name, stats_list, n_particles, precision, launches=p["launches"])
     secs = p["ms"] / 1e3
-    traffic = vcycle_traffic(traffic_key) if (traffic_key and name == "vcycle") else None
+    traffic = kernel_traffic(name, traffic_key) if traffic_key else None
     base = {"kernel": name, "traffic": traffic,
-            "traffic_unit": "DRAM bytes per V-cycle (ncu)" if name == "vcycle" else None, "launches": p["launches"],
+            "traffic_unit": "DRAM bytes per V-cycle (ncu)" if name == "vcycle" else "DRAM bytes per launch (ncu)",
+            "launches": p["launches"],
             "avg_launch_ms": p["ms"] / p["launches"], "algorithmic_total": units, "algorithmic_unit": kind,
             "timed": f"CUDA events around every {name} launch, over a replay of the timed steps from their start state"}
     if kind == "flop":
@@ -308,9 +322,9 @@ def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, local, sample_clocks=Tr
     """Warm-up, one profiled breakdown step, K timed steps (the L-BFGS loop on
     the device), the same K steps of the partner precision from the same start
     state (timed alike), then a replay of the K steps with CUDA events around
-    every V-cycle (`dominant`) for the roofline, in which the partner also
-    steps from each FP64 state so that its per-step error is measured, and the
-    end-to-end pass through host buffers."""
+    every V-cycle and every fine-Hessian assembly for the rooflines, in which
+    the partner also steps from each FP64 state so that its per-step error is
+    measured, and the end-to-end pass through host buffers."""
     import torch
     from paper_1911_07913_gb300 import hot
     torch.cuda.set_device(local)
@@ -349,7 +363,7 @@ def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, local, sample_clocks=Tr
         g2.profile(False)
     if not profile_run:
         replay_state(g, sc, start_state)
-        g.profile(True, only=f"{dominant},hessian_cells")
+        g.profile(True, only="vcycle,hessian_cells")
         if g2 is not None:
             g2.profile(True, only="vcycle")
         prof_stats, errors, partner_stats = [], [], []
@@ -741,7 +755,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dominant", default="vcycle", help="kernel timed live for the roofline entry")
+    ap.add_argument("--dominant", default="auto",
+                    help="kernel of the roofline entry (auto: the top kernel of the launch list, the fine Hessian "
+                         "assembly in FP64, the V-cycle in mixed precision)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision arms")
     ap.add_argument("--no-2m", action="store_true", help="skip the 2M-particle FP64 / mixed pair")
     ap.add_argument("--no-e2e", action="store_true")
@@ -806,10 +822,14 @@ def main():
     t_max = max_over_ranks(r["total_ms"], ws)
     value = credited_rate(sc.n, r["stats"], t_max, ws)
     prec_key = "fp64" if opts.precision == 0 else "mixed"
-    roof = roofline_entry(args.dominant, r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
-                          traffic_key=f"{args.workload}_{prec_key}_l{opts.levels}_bytes_per_vcycle", fp64_probe=probe)
+    roof_vc = roofline_entry("vcycle", r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
+                             traffic_key=f"{args.workload}_{prec_key}_l{opts.levels}_bytes_per_vcycle",
+                             fp64_probe=probe)
     roof_hess = roofline_entry("hessian_cells", r["prof"], r["prof_stats"], sc.n, opts.precision, peaks,
+                               traffic_key=f"{args.workload}_{prec_key}_bytes_per_launch",
                                fp64_probe=probe) if opts.precision == 0 else None
+    dominant = args.dominant if args.dominant != "auto" else ("hessian_cells" if opts.precision == 0 else "vcycle")
+    roof = roof_hess if dominant == "hessian_cells" else roof_vc
     mixed = {}
     if partner is not None and "partner" in r and opts.precision == 0:
         mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_l{opts.levels}_bytes_per_vcycle", ws)
@@ -851,7 +871,7 @@ def main():
             "per_step": rec, "warmup_status": [int(s["status"]) for s in r["warm"]],
             "p50_ms": float(np.percentile(sm, 50)), "p99_ms": float(np.percentile(sm, 99)),
             "e2e": e2e, "gpu_launches": int(r["launches"]), "roofline": roof,
-            "roofline_hessian_assembly": roof_hess,
+            "roofline_vcycle": roof_vc, "roofline_hessian_assembly": roof_hess,
             "lbfgs_loop_on_device": r["device_loop"],
             "kernel_ms_one_step": {k: round(v["ms"], 3) for k, v in r["breakdown"].items()},
             "clocks": r["clocks"], "fp64_probe_tflops": probe, "mixed": mixed or None,

@@ -134,3 +134,35 @@ def test_hessian_roofline_counts_every_build():
     flop = 2 * (27 * 27 * 3 + 378 * 9 * 3) * 1000 * 5
     assert r["algorithmic_total"] == flop and r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(flop / 10e-3 / 1e12)
+
+
+def test_kernel_traffic_is_pinned_to_its_source(tmp_path, monkeypatch):
+    """The ncu DRAM figure is reported only while the kernel's source file
+    hashes to the value recorded beside it; otherwise traffic is null."""
+    import hashlib
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_1911_07913_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "elastic.cu").write_bytes(b"kernel source v1")
+    sha = hashlib.sha256(b"kernel source v1").hexdigest()
+    (tmp_path / "profiles" / "hessian_cells_dram.txt").write_text(
+        f"# comment: not a value\nelastic_cu_sha256: {sha}\ntwo_bars_600k_fp64_bytes_per_launch: 1234\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("hessian_cells", "two_bars_600k_fp64_bytes_per_launch") == 1234.0
+    assert bench.kernel_traffic("hessian_cells", "missing_key") is None
+    assert bench.kernel_traffic("vcycle", "two_bars_600k_fp64_l5_bytes_per_vcycle") is None   # no summary file
+    (csrc / "elastic.cu").write_bytes(b"kernel source v2")
+    assert bench.kernel_traffic("hessian_cells", "two_bars_600k_fp64_bytes_per_launch") is None
+
+
+def test_committed_traffic_summaries_parse():
+    """Both committed summaries carry a source hash and the keys bench.py
+    asks for."""
+    for name, (summary, source) in bench.TRAFFIC_FILES.items():
+        lines = open(os.path.join(ROOT, "profiles", summary)).read().splitlines()
+        kv = dict(line.split(": ", 1) for line in lines if ": " in line and not line.startswith("#"))
+        assert len(kv[source.replace(".", "_") + "_sha256"]) == 64
+    kv = dict(line.split(": ", 1) for line in open(os.path.join(ROOT, "profiles", "vcycle_dram.txt")).read().splitlines()
+              if ": " in line and not line.startswith("#"))
+    assert float(kv["two_bars_600k_fp64_l5_bytes_per_vcycle"]) > 1e9
+    assert float(kv[f"two_bars_2m_mixed_l{bench.LEVELS_2M}_bytes_per_vcycle"]) > 1e9
