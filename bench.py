@@ -442,8 +442,10 @@ def run_batching(seed, steps, count=64):
     tuned = hot.batch_autotune(gs, 1)     # launch configuration: more (ordinary) steps
     f = tuned["flags"]
     tuned["launch"] = ("V-cycle graph, cooperative sweeps" if not f & 1 else
-                       "eager V-cycle, one launch per color" if f & 4 else "eager V-cycle, cooperative sweeps")
-    if f & 4:
+                       "eager V-cycle, one launch per color" if f & 4 else
+                       "eager V-cycle, one launch per color on the finest level, cluster or cooperative sweeps on "
+                       "the others" if f & 8 else "eager V-cycle, cooperative sweeps")
+    if f & 12:
         tuned["sweep_rows_per_block"] = (8, 2, 4, 16)[(f >> 8) & 3]
     torch.cuda.synchronize()
     t0 = time.perf_counter()

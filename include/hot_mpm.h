@@ -310,13 +310,15 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
  * `steps` real batched steps under each candidate -- the V-cycle as a CUDA
  * graph with one cooperative launch per smoothing sweep (options bits 0 and
  * 2 clear), the V-cycle launched eagerly (bit 0), eagerly with one launch
- * per Gauss-Seidel color (bits 0 and 2) with 2, 4, 8 or 16 rows per block
- * (bits 8-9) -- with half, all and twice the host cores as worker threads,
- * then keeps the fastest: the scenes' bits 0, 2, 8 and 9 are set to it and
- * mpm_step_batch uses its worker count from then on.  The candidates differ
- * in launch shape only, so the tuning steps are ordinary steps of the scenes
- * (steps x 6 x the number of distinct worker counts).  Outputs (may be NULL): the chosen bits, workers, particle-steps/s
- * and the number of steps each scene took while tuning. */
+ * per Gauss-Seidel color on every level (bits 0 and 2) or on the finest
+ * level only (bits 0 and 3), each with 2, 4, 8 or 16 rows per block of
+ * those launches (bits 8-9) -- with half, all and twice the host cores as
+ * worker threads, then keeps the fastest: the scenes' bits 0, 2, 3, 8 and 9
+ * are set to it and mpm_step_batch uses its worker count from then on.  The
+ * candidates differ in launch shape only, so the tuning steps are ordinary
+ * steps of the scenes (steps x 10 x the number of distinct worker counts).
+ * Outputs (may be NULL): the chosen bits, workers, particle-steps/s and the
+ * number of steps each scene took while tuning. */
 mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int32_t *flags_out,
                               int32_t *workers_out, double *rate_out, int32_t *steps_run_out);
 

@@ -843,8 +843,10 @@ mpm_status mpm_step_batch(mpm_scene_t *scenes, int32_t n, mpm_step_stats *stats)
 // default); V-cycle launched eagerly (no per-step graph capture, which
 // serialises host threads); eager with one launch per color (no cooperative
 // launches, whose co-residency requirement keeps small scenes' kernels from
-// overlapping).  None changes the arithmetic.
-static const int32_t kTuneModes[3] = {0, 1, 5};
+// overlapping); eager with one launch per color on the finest level only (the
+// coarser levels of small scenes then sweep as 16-CTA cluster launches, which
+// overlap with other scenes' kernels).  None changes the arithmetic.
+static const int32_t kTuneModes[4] = {0, 1, 5, 9};
 
 mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int32_t *flags_out,
                               int32_t *workers_out, double *rate_out, int32_t *steps_run_out) {
@@ -868,12 +870,12 @@ mpm_status mpm_batch_autotune(mpm_scene_t *scenes, int32_t n, int32_t steps, int
   // sweeps (bits 8-9, only where those launches run) x worker threads
   std::vector<int> cand;
   for (int mode : kTuneModes) {
-    if (mode & 4)
+    if (mode & 12)
       for (int wb = 0; wb < 4; ++wb) cand.push_back(mode | (wb << 8));
     else
       cand.push_back(mode);
   }
-  const int kTuned = 5 | (3 << 8);
+  const int kTuned = 1 | 4 | 8 | (3 << 8);
   double best = -1.0;
   int best_mode = 0, best_w = cores, runs = 0;
   for (int mode : cand) {

@@ -487,7 +487,7 @@ def test_batch_autotune_steps_are_ordinary_steps(hot):
     plain = [hot.HotScene(sc, opts) for sc in scs]
     choice = hot.batch_autotune(tuned, 1)
     f = choice["flags"]
-    assert (f & 5) in (0, 1, 5) and (f >> 8 == 0 or f & 4) and f & ~(5 | (3 << 8)) == 0
+    assert (f & 13) in (0, 1, 5, 9) and (f >> 8 == 0 or f & 12) and f & ~(13 | (3 << 8)) == 0
     assert choice["workers"] >= 1 and choice["particle_steps_per_s"] > 0
     for g in plain:
         for _ in range(choice["steps_run"]):
