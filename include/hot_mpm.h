@@ -127,7 +127,7 @@ typedef struct {
                             bit 3: one launch per color on the finest level only (by default
                             each symmetric sweep of each level is one cooperative launch, or
                             one 16-CTA cluster launch with hardware cluster barriers between
-                            colors on levels with at most 144 (FP64) or 192 (FP32) rows per
+                            colors on levels with at most 160 (FP64) or 256 (FP32) rows per
                             color whose u fits in shared memory, 64 otherwise);
                             bit 6: cooperative launches on those levels too (bits 2, 3 and 6
                             change launch boundaries only, not the arithmetic);
@@ -138,6 +138,10 @@ typedef struct {
                             bit 10: cluster-launched sweeps read and write u in global memory
                             (by default each CTA of the cluster holds the level's u in shared
                             memory and writes new values into every CTA's copy; same results);
+                            bit 11: with u in shared memory, a hardware cluster barrier between
+                            colors (by default each CTA waits on its own mbarrier for the bytes
+                            of the color's rows, sent by remote stores that count them; same
+                            results);
                             bit 4: drive the L-BFGS iterations from the host;
                             bit 5: run them as one CUDA graph whose conditional nodes take every
                             decision on the device (by default the graph is used once the

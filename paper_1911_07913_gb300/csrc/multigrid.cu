@@ -937,6 +937,142 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_cluster_smem(SweepPlan plan, c
   for (int k = rank * SW_NT + threadIdx.x; k < 3 * n; k += G * SW_NT) u[k] = su[k];
 }
 
+// Distributed-shared-memory helpers (PTX): 32-bit shared-window addresses,
+// their image in another CTA of the cluster, mbarriers with transaction
+// counts, and remote stores that report their bytes to the receiving CTA's
+// mbarrier.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void st_async_tx(uint32_t addr, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+               "r"(__float_as_uint(v)), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_tx(uint32_t addr, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+               "l"(__double_as_longlong(v)), "r"(bar)
+               : "memory");
+}
+
+// The same sweep as k_sgs_cluster_smem without a cluster-wide barrier between
+// colors.  Each CTA owns two mbarriers, used by alternate colors.  A row's
+// warp sends the row's new u_i to every CTA's copy with remote stores that
+// count their bytes on the receiving CTA's mbarrier of that color; each CTA
+// expects exactly (rows of the color) x 3 values and waits only for them, so
+// no CTA waits for a fence of all outstanding stores.  Ordering: a CTA starts
+// color k+1 only after every row of color k, from every CTA, has arrived; the
+// rows of color k were computed (and their neighbours read) before they were
+// sent, so no value of color k+1 can overwrite one still to be read for
+// color k, and a CTA is at most one color ahead of another, which the two
+// alternating mbarriers cover.  Waits are bounded: past the scene's poll
+// limit the timeout is recorded and the wait goes on (the bytes of a color
+// always arrive), and past max(limit, 2^22) polls the CTA stops.
+template <class T>
+__global__ void __launch_bounds__(SW_NT, 1) k_sgs_cluster_tx(SweepPlan plan, const int4 *__restrict__ rec,
+                                                             const int *__restrict__ cols, const T *__restrict__ vals,
+                                                             const T *__restrict__ dinv, const T *__restrict__ b,
+                                                             T *u, int n, int *err, long long spin_limit) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ int4 s_rec[54][SW_WARPS];
+  __shared__ __align__(8) unsigned long long s_bar[2];
+  extern __shared__ __align__(16) unsigned char sw_dyn[];
+  T *su = reinterpret_cast<T *>(sw_dyn);
+  const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (int)cluster.block_rank();
+  const int first = blockIdx.x + G * warp;
+  for (int k = lane; k < plan.steps; k += 32) {
+    int4 rr = first < plan.nr[k] ? rec[plan.off[k] + first] : make_int4(-1, 0, 0, 0);
+    if (k >= plan.low_steps) rr.w = rr.z;
+    s_rec[k][warp] = rr;
+  }
+  for (int k = threadIdx.x; k < 3 * n; k += SW_NT) su[k] = u[k];
+  const uint32_t bar0 = smem_addr(&s_bar[0]), bar1 = smem_addr(&s_bar[1]);
+  if (threadIdx.x == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    mbar_init_fence();
+  }
+  // every CTA's barriers are initialised and its copy loaded before any remote store
+  cluster.sync();
+  // lanes < G send to CTA `lane`: its copy of u and its two barriers
+  uint32_t dst_u = 0, dst_b0 = 0, dst_b1 = 0;
+  if (lane < G) {
+    dst_u = cluster_addr(smem_addr(su), (uint32_t)lane);
+    dst_b0 = cluster_addr(bar0, (uint32_t)lane);
+    dst_b1 = cluster_addr(bar1, (uint32_t)lane);
+  }
+  const long long hard = spin_limit > (1ll << 22) ? spin_limit : (1ll << 22);
+  bool live = true;
+  RowRegs<T> R;
+  {
+    const int4 r0 = s_rec[0][warp];
+    if (r0.x >= 0) load_row<T>(R, r0.x, r0.y, r0.z, r0.w, lane, cols, vals, dinv, b);
+  }
+  for (int k = 0; k < plan.steps; ++k) {
+    const uint32_t bar = (k & 1) ? bar1 : bar0;
+    if (threadIdx.x == 0 && live) mbar_expect_tx(bar, (uint32_t)(plan.nr[k] * 3 * (int)sizeof(T)));
+    const int4 r = s_rec[k][warp];
+    if (r.x >= 0) {   // warp-uniform
+      const T val = row_new_u<T, false>(R, r.x, r.y, r.z, r.w, lane, cols, vals, su);
+      const T w0 = __shfl_sync(0xffffffffu, val, 0), w1 = __shfl_sync(0xffffffffu, val, 1),
+              w2 = __shfl_sync(0xffffffffu, val, 2);
+      if (lane < G && live) {
+        const uint32_t a = dst_u + (uint32_t)(3 * r.x * (int)sizeof(T)), mb = (k & 1) ? dst_b1 : dst_b0;
+        st_async_tx(a, w0, mb);
+        st_async_tx(a + (uint32_t)sizeof(T), w1, mb);
+        st_async_tx(a + 2u * (uint32_t)sizeof(T), w2, mb);
+      }
+    }
+    if (k + 1 < plan.steps) {   // the next color's row does not depend on u: load it while waiting
+      const int4 rn = s_rec[k + 1][warp];
+      if (rn.x >= 0) load_row<T>(R, rn.x, rn.y, rn.z, rn.w, lane, cols, vals, dinv, b);
+    }
+    if (live) {
+      const uint32_t parity = (uint32_t)((k >> 1) & 1);
+      long long spins = 0;
+      while (!mbar_test_wait_cluster(bar, parity)) {
+        ++spins;
+        if (spins == spin_limit && threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+        if (spins > hard) {
+          live = false;
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          break;
+        }
+        if ((spins & 63) == 0) __nanosleep(128);
+      }
+    }
+  }
+  // every CTA has received every value (no store is in flight); no CTA
+  // touches another's shared memory after this
+  cluster.sync();
+  for (int k = rank * SW_NT + threadIdx.x; k < 3 * n; k += G * SW_NT) u[k] = su[k];
+}
+
 template <class T>
 __global__ void __launch_bounds__(NT) k_coarse_pcg(int64_t n, const int *__restrict__ row_ptr, const int *__restrict__ cols,
                                                    const T *__restrict__ vals, const T *__restrict__ diag,
@@ -1360,12 +1496,15 @@ int persistent_blocks() {
 // Row limits (largest color of the level), measured per level on the two-bar
 // scenes against the grid-barrier sweep: with u in global memory the cluster
 // sweep wins up to a few dozen FP64 rows per color; with u in shared memory
-// (10-25% faster than in global memory on those levels) FP64 levels win up
-// to ~150 rows per color (135: 11% faster; 234: 57% slower, the FP64 pipe of
-// 16 SMs), FP32 levels up to ~200 (135: 11% faster; 234: 6% slower).
+// and byte counts between colors (k_sgs_cluster_tx) FP64 levels win up to
+// ~160 rows per color (135: 20% faster; 234: 50% slower, the FP64 pipe of 16
+// SMs) and FP32 levels up to the cluster's 256 warps (234: 15% faster); with
+// the cluster barrier between colors (k_sgs_cluster_smem) FP32 levels win up
+// to ~200 rows (135: 11% faster; 234: 6% slower).
 constexpr int CLUSTER_SWEEP_ROWS = 64;
-constexpr int CLUSTER_SWEEP_ROWS_SMEM = 144;   // FP64, u in shared memory
+constexpr int CLUSTER_SWEEP_ROWS_SMEM = 160;      // FP64, u in shared memory
 constexpr int CLUSTER_SWEEP_ROWS_FP32 = 192;
+constexpr int CLUSTER_SWEEP_ROWS_FP32_TX = 256;   // FP32, u in shared memory, byte counts between colors
 template <class T>
 int sweep_cluster_size() {
   static std::atomic<int> cached{-1};
@@ -1407,34 +1546,43 @@ size_t sweep_smem_limit() {
   if (c < 0) {
     c = 0;
     const int cl = sweep_cluster_size<T>();
+    // both shared-memory sweeps (barrier and transaction-count forms) must fit
+    const void *kern[2] = {(const void *)k_sgs_cluster_smem<T>, (const void *)k_sgs_cluster_tx<T>};
     if (cl > 0) {
-      if (cudaFuncSetAttribute(k_sgs_cluster_smem<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-          cudaSuccess)
-        cudaGetLastError();
+      for (const void *f : kern)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+          cudaGetLastError();
       for (int kb : {192, 160, 128, 96, 64, 48}) {
         const int bytes = kb * 1024;
-        if (cudaFuncSetAttribute(k_sgs_cluster_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
-            cudaSuccess) {
-          cudaGetLastError();
-          continue;
+        bool fits = true;
+        for (const void *f : kern) {
+          if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            fits = false;
+            break;
+          }
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3(cl);
+          cfg.blockDim = dim3(SW_NT);
+          cfg.dynamicSmemBytes = bytes;
+          cudaLaunchAttribute attr[1];
+          attr[0].id = cudaLaunchAttributeClusterDimension;
+          attr[0].val.clusterDim.x = cl;
+          attr[0].val.clusterDim.y = 1;
+          attr[0].val.clusterDim.z = 1;
+          cfg.attrs = attr;
+          cfg.numAttrs = 1;
+          int nc = 0;
+          if (cudaOccupancyMaxActiveClusters(&nc, f, &cfg) != cudaSuccess || nc < 1) {
+            cudaGetLastError();
+            fits = false;
+            break;
+          }
         }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(cl);
-        cfg.blockDim = dim3(SW_NT);
-        cfg.dynamicSmemBytes = bytes;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cl;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, k_sgs_cluster_smem<T>, &cfg) == cudaSuccess && nc >= 1) {
+        if (fits) {
           c = bytes;
           break;
         }
-        cudaGetLastError();
       }
     }
     cached.store(c);
@@ -1450,7 +1598,9 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
   // the level's u in shared memory unless it does not fit (or flag bit 10)
   const size_t smem = 3 * (size_t)t.n * sizeof(T);
   const bool in_smem = !(s.opts.flags & 1024) && smem <= sweep_smem_limit<T>();
-  const int row_limit = sizeof(T) == 4 ? CLUSTER_SWEEP_ROWS_FP32 : in_smem ? CLUSTER_SWEEP_ROWS_SMEM : CLUSTER_SWEEP_ROWS;
+  const bool tx = in_smem && !(s.opts.flags & 2048);
+  const int row_limit = sizeof(T) == 4 ? (tx ? CLUSTER_SWEEP_ROWS_FP32_TX : CLUSTER_SWEEP_ROWS_FP32)
+                                       : in_smem ? CLUSTER_SWEEP_ROWS_SMEM : CLUSTER_SWEEP_ROWS;
   if (CLR > 0 && !(s.opts.flags & 64) && max_rows <= std::min(row_limit, CLR * SW_WARPS)) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CLR);
@@ -1465,10 +1615,17 @@ void launch_sgs_persistent(Scene &s, Topo &t, Vals<T> &V, Hier<T> &h, const Swee
     cfg.numAttrs = 1;
     if (in_smem) {
       cfg.dynamicSmemBytes = smem;
-      HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_cluster_smem<T>, plan, (const int4 *)t.color_rec.p,
-                                  (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p, (const T *)V.b.p,
-                                  V.u.p, (int)t.n));
-      note_launch("k_sgs_cluster_smem");
+      if (!tx) {   // hardware cluster barrier between colors
+        HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_cluster_smem<T>, plan, (const int4 *)t.color_rec.p,
+                                    (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p,
+                                    (const T *)V.b.p, V.u.p, (int)t.n));
+        note_launch("k_sgs_cluster_smem");
+      } else {   // per-CTA transaction counts between colors
+        HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_cluster_tx<T>, plan, (const int4 *)t.color_rec.p,
+                                    (const int *)t.cols.p, (const T *)V.vals.p, (const T *)V.dinv.p,
+                                    (const T *)V.b.p, V.u.p, (int)t.n, s.errflag.p, s.spin_limit));
+        note_launch("k_sgs_cluster_tx");
+      }
       return;
     }
     HOT_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_persistent<T, false, true>, plan, (const int4 *)t.color_rec.p,

@@ -107,7 +107,8 @@ class SolverOptions:
                               # 4: host-driven L-BFGS loop; 5: device-side graph loop always;
                               # 6: no cluster-launched sweeps on levels with few rows per color;
                               # 7: half-matrix residual; 8-9: rows per block of per-color launches;
-                              # 10: cluster sweeps with u in global instead of shared memory
+                              # 10: cluster sweeps with u in global instead of shared memory;
+                              # 11: cluster barrier instead of per-CTA byte counts between colors
     solver: int = 0           # 0: HOT (Alg. 3); 1: PN-PCG; 2: PN-MGPCG (Alg. 1, comparison solvers)
     refresh_every: int = 0    # HOT extension: rebuild the hierarchy at the iterate every k iterations (0: off)
     fallback_after: int = 0   # HOT extension: finish an unconverged step with PN-MGPCG after k iterations

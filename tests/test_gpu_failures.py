@@ -138,3 +138,29 @@ def test_device_wait_timeout_is_reported_and_scene_recovers(hot):
                   skipped=tr["skipped"], fallback=tr["fallback"])
     dvo, _ = O.hot_solve(O.Problem(sc, og, st["dt"]), opts, replay=rep)
     assert np.abs(dv - dvo).max() <= 1e-9 * np.abs(dvo).max()
+
+
+def test_cluster_sweep_wait_past_limit_is_reported_and_completes(hot):
+    """The cluster sweeps that keep u in shared memory wait on per-CTA byte
+    counts; past the poll limit they record the timeout but keep waiting
+    (the bytes of a color always arrive), so no CTA leaves while stores into
+    its shared memory may be in flight.  With the limit cut to one poll and
+    the default launches, the V-cycle reports MPM_ERR_TIMEOUT (or completes
+    within one poll per wait); with the default limit back the scene applies
+    the same V-cycle, bitwise, as before the limit was cut."""
+    sc = scenes.two_bars_scene(seed=4, res=64, width=6, length=14, gap=8, E_a=1e5, E_b=1e8)
+    opts = scenes.SolverOptions(eps=1e-7, cn_mode=0, levels=3, flags=1)   # eager: each launch on its own
+    g = hot.HotScene(sc, opts)
+    g.p2g()
+    g.build_hierarchy()
+    b = np.random.default_rng(7).normal(size=(len(g.grid()["m"]), 3))
+    u_ref, its_ref = g.vcycle(b)
+    g.set_wait_limit(1)
+    try:
+        g.vcycle(b)
+    except hot.HotError as e:
+        assert e.code == 10 and "timed out" in str(e)     # MPM_ERR_TIMEOUT
+    g.set_wait_limit(1 << 24)
+    u, its = g.vcycle(b)
+    assert its == its_ref and np.array_equal(u, u_ref)
+    g.close()

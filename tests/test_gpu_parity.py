@@ -143,14 +143,15 @@ def test_vcycle_matches_oracle_with_same_coarse_count(hot, name):
     assert abs(vc2.cg_counts[0] - its) <= 1
 
 
-@pytest.mark.parametrize("flags", [4, 0, 8, 64, 128, 1024, 4 | (1 << 8), 4 | (3 << 8)])
+@pytest.mark.parametrize("flags", [4, 0, 8, 64, 128, 1024, 2048, 4 | (1 << 8), 4 | (3 << 8)])
 def test_vcycle_smoothing_launch_modes(hot, flags):
     """One launch per color (bit 2), one launch per sweep (default: a cluster
     launch on levels whose colors fit a cluster's warps, else cooperative),
     per-color launches on the finest level only (bit 3), cooperative
     launches on every level (bit 6), the residual read from half of the
-    symmetric matrix (bit 7, the transposed half by atomics) and cluster
-    sweeps with u in global memory (bit 10) apply the same V-cycle."""
+    symmetric matrix (bit 7, the transposed half by atomics), cluster
+    sweeps with u in global memory (bit 10) and with a cluster barrier
+    between colors (bit 11) apply the same V-cycle."""
     sc, opts = SCENES["bars_nh_cn"]
     opts = scenes.SolverOptions(**{**opts.__dict__, "flags": flags})
     g = hot.HotScene(sc, opts)
@@ -173,9 +174,10 @@ def test_vcycle_launch_modes_bitwise(hot, precision):
     """Every sweep launch mode runs the same per-row arithmetic in the same
     color order: on one hierarchy, the V-cycle's output is bitwise the same
     with the default launches (cluster sweeps on levels with few rows per
-    color, u in shared memory), cluster sweeps with u in global memory
-    (bit 10), cooperative sweeps on every level (bit 6) and one launch per
-    color (bit 2)."""
+    color, u in shared memory, per-CTA byte counts between colors), with a
+    cluster barrier between colors (bit 11), cluster sweeps with u in global
+    memory (bit 10), cooperative sweeps on every level (bit 6) and one launch
+    per color (bit 2)."""
     sc, opts = SCENES["bars_nh_cn"]
     base = {**opts.__dict__, "precision": precision}
     g = hot.HotScene(sc, scenes.SolverOptions(**base))
@@ -183,7 +185,7 @@ def test_vcycle_launch_modes_bitwise(hot, precision):
     g.build_hierarchy()
     b = np.random.default_rng(5).normal(size=(len(g.grid()["m"]), 3))
     out = []
-    for flags in (0, 1024, 64, 4):
+    for flags in (0, 2048, 1024, 64, 4):
         g.set_options(scenes.SolverOptions(**{**base, "flags": flags}))
         out.append(g.vcycle(b))
     g.close()
