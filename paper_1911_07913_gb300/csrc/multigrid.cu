@@ -956,14 +956,17 @@ __device__ __forceinline__ void mbar_init_fence() {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_test_wait_cluster(uint32_t bar, uint32_t parity) {
+// waits in hardware (the thread is suspended, up to about `hint_ns`, so it
+// takes no issue slots from warps still computing) for the phase of the
+// given parity; false if it has not completed by then
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
   uint32_t done;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(done)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
       : "memory");
   return done != 0;
 }
@@ -990,7 +993,8 @@ __device__ __forceinline__ void st_async_tx(uint32_t addr, double v, uint32_t ba
 // color k, and a CTA is at most one color ahead of another, which the two
 // alternating mbarriers cover.  Waits are bounded: past the scene's poll
 // limit the timeout is recorded and the wait goes on (the bytes of a color
-// always arrive), and past max(limit, 2^22) polls the CTA stops.
+// always arrive), and past max(limit, 2^22) polls (each a hardware wait of
+// about a microsecond at most) the CTA stops.
 template <class T>
 __global__ void __launch_bounds__(SW_NT, 1) k_sgs_cluster_tx(SweepPlan plan, const int4 *__restrict__ rec,
                                                              const int *__restrict__ cols, const T *__restrict__ vals,
@@ -1055,7 +1059,7 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_cluster_tx(SweepPlan plan, con
     if (live) {
       const uint32_t parity = (uint32_t)((k >> 1) & 1);
       long long spins = 0;
-      while (!mbar_test_wait_cluster(bar, parity)) {
+      while (!mbar_try_wait_cluster(bar, parity, 1000u)) {
         ++spins;
         if (spins == spin_limit && threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
         if (spins > hard) {
@@ -1063,7 +1067,6 @@ __global__ void __launch_bounds__(SW_NT, 1) k_sgs_cluster_tx(SweepPlan plan, con
           atomicOr(err, DEV_ERR_TIMEOUT);
           break;
         }
-        if ((spins & 63) == 0) __nanosleep(128);
       }
     }
   }
