@@ -213,10 +213,6 @@ def kernel_traffic(name, key):
     return float(v) if v else None
 
 
-def vcycle_traffic(key):
-    return kernel_traffic("vcycle", key)
-
-
 def roofline_entry(name, prof, stats_list, n_particles, precision, peaks, traffic_key=None, fp64_probe=None):
     """Dominant-kernel roofline from live CUDA-event times over the timed steps."""
     p = prof.get(name)
@@ -317,7 +313,7 @@ def mixed_error(c64, v64, x64, c32, v32, x32, x_prev, dx, m=None, vp64=None, vp3
     return out
 
 
-def run_gpu(sc, opts, steps, warmup, dominant, with_e2e, local, sample_clocks=True, profile_run=False,
+def run_gpu(sc, opts, steps, warmup, with_e2e, local, sample_clocks=True, profile_run=False,
             partner_opts=None, fp64_probe=None):
     """Warm-up, one profiled breakdown step, K timed steps (the L-BFGS loop on
     the device), the same K steps of the partner precision from the same start
@@ -817,7 +813,7 @@ def main():
     if not args.no_mixed and args.workload != "cube8k":
         partner = workload_opts(1 - args.precision, args.refresh, opts.levels)
     barrier(ws)
-    r = run_gpu(sc, opts, args.steps, args.warmup, args.dominant, not args.no_e2e, local,
+    r = run_gpu(sc, opts, args.steps, args.warmup, not args.no_e2e, local,
                 sample_clocks=not args.profile_run, profile_run=args.profile_run, partner_opts=partner,
                 fp64_probe=probe)
     barrier(ws)
@@ -837,8 +833,8 @@ def main():
         mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_l{opts.levels}_bytes_per_vcycle", ws)
     if partner is not None and not args.no_2m and args.workload == "two_bars_600k" and opts.precision == 0:
         sc2 = scenes.two_bars_2m_scene(seed=rank)
-        r2 = run_gpu(sc2, workload_opts(0, args.refresh, args.levels_2m), args.steps, args.warmup, "vcycle", False,
-                     local, partner_opts=workload_opts(1, args.refresh, args.levels_2m), fp64_probe=probe)
+        r2 = run_gpu(sc2, workload_opts(0, args.refresh, args.levels_2m), args.steps, args.warmup, False, local,
+                     partner_opts=workload_opts(1, args.refresh, args.levels_2m), fp64_probe=probe)
         mixed["two_bars_2m"] = summarize_pair(r2, sc2, peaks, f"two_bars_2m_mixed_l{args.levels_2m}_bytes_per_vcycle", ws)
         mixed["two_bars_2m"]["roofline_fp64_vcycle"] = roofline_entry(
             "vcycle", r2["prof"], r2["prof_stats"], sc2.n, 0, peaks, fp64_probe=probe)
