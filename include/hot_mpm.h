@@ -126,9 +126,9 @@ typedef struct {
                             bit 2: one launch per Gauss-Seidel color on every level;
                             bit 3: one launch per color on the finest level only (by default
                             each symmetric sweep of each level is one cooperative launch, or
-                            one 16-CTA cluster launch with hardware cluster barriers between
-                            colors on levels with at most 160 (FP64) or 256 (FP32) rows per
-                            color whose u fits in shared memory, 64 otherwise);
+                            one 16-CTA cluster launch (bits 10 and 11) on levels with at most
+                            160 (FP64) or 256 (FP32) rows per color whose u fits in shared
+                            memory, 64 otherwise);
                             bit 6: cooperative launches on those levels too (bits 2, 3 and 6
                             change launch boundaries only, not the arithmetic);
                             bit 7: residual from half of the symmetric matrix (prefix blocks and
