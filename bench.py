@@ -188,6 +188,52 @@ def algorithmic_units(name: str, stats_list, n_particles: int, precision: int, l
     return 40 * visits, "byte"
 
 
+def step_traffic(stats_list, precision: int, refresh: int) -> int:
+    """Algorithmic HBM bytes of whole steps, summed over stats_list:
+    P2G 128 B per particle (x, v, C, m) + 32 B per node (m, m v written);
+    G2P 288 B per particle (x, F read; x, v, C, F written) + 24 B per node;
+    every energy evaluation (the one at dv = 0 and each line-search trial)
+    112 B per particle + 48 B per node; every gradient (at dv = 0 and after
+    each iteration) 112 B per particle + 72 B per node; the two-loop 66 vector
+    passes of 24 B per node per iteration (window 8); each V-cycle its block
+    visits (as in algorithmic_units) at 76 B (FP64: 72 B of values and a
+    column index) or 40 B (FP32); each hierarchy build (at the first
+    iteration, and again every `refresh` iterations) the per-particle
+    stiffness (45 values) written and read, the fine matrix written, and
+    every Galerkin level's finer matrix read and its own written."""
+    vb = 76 if precision == 0 else 40
+    bb = 72 if precision == 0 else 36
+    sb = 8 if precision == 0 else 4
+    total = 0
+    for st in stats_list:
+        npart, n0, its, trials = st["n_particles"], st["n_nodes"][0], st["iters"], st["ls_trials"]
+        nnz, nodes, nl = st["nnz_blocks"], st["n_nodes"], st["n_levels"]
+        total += 128 * npart + 32 * n0 + 288 * npart + 24 * n0
+        total += (1 + trials) * (112 * npart + 48 * n0)
+        total += (1 + its) * (112 * npart + 72 * n0)
+        total += its * 66 * 24 * n0
+        visits = sum((7 * (nnz[m] - nodes[m])) // 2 + nnz[m] for m in range(nl - 1))
+        total += st["vcycles"] * visits * vb
+        builds = 0 if its == 0 else 1 + ((its - 1) // refresh if refresh > 0 else 0)
+        build = 2 * 45 * sb * npart + nnz[0] * bb + sum((nnz[m] + nnz[m + 1]) * bb for m in range(nl - 1))
+        total += builds * build
+    return total
+
+
+def step_hbm_entry(stats_list, precision, refresh, total_ms, peaks):
+    """Whole-step achieved bandwidth: step_traffic over the timed steps' time."""
+    if not stats_list or total_ms <= 0:
+        return None
+    b = step_traffic(stats_list, precision, refresh)
+    achieved = b / (total_ms / 1e3) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    return {"bytes_per_step": b / len(stats_list), "achieved": achieved, "unit": "GB/s", "peak": hbm,
+            "frac": achieved / hbm, "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback",
+            "note": "algorithmic bytes of the whole step (P2G, energies, gradients, two-loop, V-cycles, hierarchy "
+                    "builds, G2P) over the device time of the timed steps; the FP64 step is bound by the FP64 "
+                    "pipe, not by these bytes"}
+
+
 # committed ncu DRAM figures per roofline unit: summary file and the source file whose hash pins them
 TRAFFIC_FILES = {"vcycle": ("vcycle_dram.txt", "multigrid.cu"),
                  "hessian_cells": ("hessian_cells_dram.txt", "elastic.cu")}
@@ -713,20 +759,21 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def summarize_pair(r, sc, peaks, traffic_key_mixed, ws=1):
+def summarize_pair(r, sc, peaks, traffic_key_mixed, ws=1, refresh=REFRESH):
     """FP64 against mixed precision on one scene from the same start state:
     throughput (converged steps only), per-step status, and the mixed step's
     error against the FP64 step from the same state."""
-    def arm(stats, step_ms, total_ms):
+    def arm(stats, step_ms, total_ms, precision):
         rec = step_record(stats, step_ms)
         sm = sorted(step_ms)
         return {"value": credited_rate(sc.n, stats, total_ms, ws), "unit": UNIT, "ms_per_step": total_ms / len(stats),
                 "p50_ms": float(np.percentile(sm, 50)), "p99_ms": float(np.percentile(sm, 99)),
-                "converged_steps": rec["converged"], "steps": rec["steps"], "per_step": rec}
+                "converged_steps": rec["converged"], "steps": rec["steps"], "per_step": rec,
+                "step_hbm": step_hbm_entry(stats, precision, refresh, total_ms, peaks)}
     p = r["partner"]
     out = {"workload": sc.name, "particles": sc.n, "start": "the same state (after the FP64 warm-up steps)",
-           "fp64": arm(r["stats"], r["step_ms"], r["total_ms"]),
-           "mixed": arm(p["stats"], p["step_ms"], p["total_ms"])}
+           "fp64": arm(r["stats"], r["step_ms"], r["total_ms"], 0),
+           "mixed": arm(p["stats"], p["step_ms"], p["total_ms"], 1)}
     f, m = out["fp64"]["value"], out["mixed"]["value"]
     out["speedup_mixed_over_fp64"] = (m / f) if f > 0 else None
     errs = p.get("errors") or []
@@ -830,12 +877,14 @@ def main():
     roof = roof_hess if dominant == "hessian_cells" else roof_vc
     mixed = {}
     if partner is not None and "partner" in r and opts.precision == 0:
-        mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_l{opts.levels}_bytes_per_vcycle", ws)
+        mixed[args.workload] = summarize_pair(r, sc, peaks, f"{args.workload}_mixed_l{opts.levels}_bytes_per_vcycle", ws,
+                                              args.refresh)
     if partner is not None and not args.no_2m and args.workload == "two_bars_600k" and opts.precision == 0:
         sc2 = scenes.two_bars_2m_scene(seed=rank)
         r2 = run_gpu(sc2, workload_opts(0, args.refresh, args.levels_2m), args.steps, args.warmup, False, local,
                      partner_opts=workload_opts(1, args.refresh, args.levels_2m), fp64_probe=probe)
-        mixed["two_bars_2m"] = summarize_pair(r2, sc2, peaks, f"two_bars_2m_mixed_l{args.levels_2m}_bytes_per_vcycle", ws)
+        mixed["two_bars_2m"] = summarize_pair(r2, sc2, peaks, f"two_bars_2m_mixed_l{args.levels_2m}_bytes_per_vcycle", ws,
+                                              args.refresh)
         mixed["two_bars_2m"]["roofline_fp64_vcycle"] = roofline_entry(
             "vcycle", r2["prof"], r2["prof_stats"], sc2.n, 0, peaks, fp64_probe=probe)
     batching = serving = solvers = None
@@ -870,6 +919,7 @@ def main():
             "p50_ms": float(np.percentile(sm, 50)), "p99_ms": float(np.percentile(sm, 99)),
             "e2e": e2e, "gpu_launches": int(r["launches"]), "roofline": roof,
             "roofline_vcycle": roof_vc, "roofline_hessian_assembly": roof_hess,
+            "step_hbm": step_hbm_entry(r["stats"], opts.precision, args.refresh, t_max, peaks),
             "lbfgs_loop_on_device": r["device_loop"],
             "kernel_ms_one_step": {k: round(v["ms"], 3) for k, v in r["breakdown"].items()},
             "clocks": r["clocks"], "fp64_probe_tflops": probe, "mixed": mixed or None,

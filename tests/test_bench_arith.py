@@ -54,7 +54,8 @@ def test_job_throughput_is_whole_job_over_slowest_rank():
 
 
 def _st(status, iters=10, norm=1e-6, dt=1e-2):
-    return {"status": status, "iters": iters, "final_norm": norm, "dt": dt}
+    return {"status": status, "iters": iters, "final_norm": norm, "dt": dt, "n_particles": 100, "n_levels": 2,
+            "nnz_blocks": [900, 60], "n_nodes": [40, 8], "ls_trials": iters, "vcycles": iters}
 
 
 def test_only_converged_steps_earn_particle_steps():
@@ -110,6 +111,7 @@ def test_pair_summary_speedup_and_error_maxima():
     assert out["speedup_mixed_over_fp64"] == pytest.approx(1.0)
     assert out["error_vs_fp64"]["max"]["grid_v_rel"] == pytest.approx(3e-6)
     assert out["mixed"]["converged_steps"] == 1
+    assert out["mixed"]["step_hbm"]["bytes_per_step"] == bench.step_traffic(stats32, 1, bench.REFRESH) / 2
 
 
 def test_reference_arm_line(capsys):
@@ -166,3 +168,28 @@ def test_committed_traffic_summaries_parse():
               if ": " in line and not line.startswith("#"))
     assert float(kv["two_bars_600k_fp64_l5_bytes_per_vcycle"]) > 1e9
     assert float(kv[f"two_bars_2m_mixed_l{bench.LEVELS_2M}_bytes_per_vcycle"]) > 1e9
+
+
+def test_step_traffic_counts_each_phase():
+    """Whole-step algorithmic bytes: the transfers once, an energy per trial
+    plus the one at dv = 0, a gradient per iteration plus the first, the
+    two-loop per iteration, each V-cycle's block visits and one hierarchy
+    build at the first iteration plus one every `refresh` iterations; a step
+    that needs no iteration builds nothing."""
+    st = {"n_particles": 1000, "n_levels": 3, "nnz_blocks": [5000, 800, 90], "n_nodes": [300, 50, 10],
+          "iters": 11, "ls_trials": 13, "vcycles": 11}
+    visits = ((7 * (5000 - 300)) // 2 + 5000) + ((7 * (800 - 50)) // 2 + 800)
+    fixed = (128 + 288) * 1000 + (32 + 24) * 300
+    energies = 14 * (112 * 1000 + 48 * 300)
+    grads = 12 * (112 * 1000 + 72 * 300)
+    twoloop = 11 * 66 * 24 * 300
+    build64 = 2 * 45 * 8 * 1000 + 5000 * 72 + (5000 + 800) * 72 + (800 + 90) * 72
+    # refresh 5: builds at the first iteration and after iterations 5 and 10
+    assert bench.step_traffic([st], 0, 5) == fixed + energies + grads + twoloop + 11 * visits * 76 + 3 * build64
+    build32 = 2 * 45 * 4 * 1000 + 5000 * 36 + (5000 + 800) * 36 + (800 + 90) * 36
+    assert bench.step_traffic([st], 1, 0) == fixed + energies + grads + twoloop + 11 * visits * 40 + build32
+    rest = {**st, "iters": 0, "ls_trials": 0, "vcycles": 0}
+    assert bench.step_traffic([rest], 0, 5) == fixed + (112 * 1000 + 48 * 300) + (112 * 1000 + 72 * 300)
+    e = bench.step_hbm_entry([st, st], 0, 5, 2.0, {"hbm_gbs": 5000.0})
+    assert abs(e["achieved"] - 2 * bench.step_traffic([st], 0, 5) / 2e-3 / 1e9) < 1e-9
+    assert abs(e["frac"] - e["achieved"] / 5000.0) < 1e-12 and e["bytes_per_step"] == bench.step_traffic([st], 0, 5)
