@@ -48,3 +48,35 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(hot, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         hot.load()
+
+
+def test_struct_field_offsets_match_header(tmp_path):
+    """Every field of every ctypes structure in the binding sits at the offset
+    a C compiler gives the field of the same name in include/hot_mpm.h, and
+    every structure has the C size: a field added, dropped, retyped or moved
+    on one side only fails here."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [hot.mpm_material, hot.mpm_bc, hot.mpm_scene_desc, hot.mpm_solver_opts, hot.mpm_step_stats]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hot_mpm.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "offsets.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "offsets"
+    include = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c99", "-I", include, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    c_layout = {(a, b): int(c) for a, b, c in (l.split() for l in out)}
+    for st in structs:
+        name = st.__name__
+        assert c_layout[(name, "sizeof")] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert c_layout[(name, field)] == getattr(st, field).offset, (name, field)
