@@ -143,6 +143,12 @@ def load(install_torch_allocator: bool = True):
     lib.mpm_server_destroy.argtypes = [C.c_void_p]
     lib.mpm_particle_energy_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(mpm_material),
                                                 C.c_int32, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p]
+    lib.mpm_set_wait_limit.argtypes = [C.c_void_p, C.c_int64]
+    lib.mpm_scene_park.argtypes = [C.c_void_p]
+    lib.mpm_scene_unpark.argtypes = [C.c_void_p]
+    lib.mpm_scene_residency.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+    lib.mpm_server_residency.argtypes = [C.c_void_p] + [C.POINTER(C.c_int64)] * 5
+    lib.mpm_probe_fp64_fma.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
     _lib = lib
     if install_torch_allocator:
         _install_torch_allocator(lib)

@@ -80,3 +80,39 @@ def test_struct_field_offsets_match_header(tmp_path):
         assert c_layout[(name, "sizeof")] == ctypes.sizeof(st), name
         for field, _ in st._fields_:
             assert c_layout[(name, field)] == getattr(st, field).offset, (name, field)
+
+
+def test_binding_argument_counts_match_header():
+    """The binding declares argument types for every function of
+    include/hot_mpm.h, as many as the header's prototype takes (an untyped
+    call would pass Python integers as C int)."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"^\s*(?:mpm_status|const char \*|int64_t|void)\s*(mpm_\w+)\s*\(([^)]*)\)\s*;", src,
+                         flags=re.M | re.S):
+        params = m.group(2).strip()
+        protos[m.group(1)] = 0 if params in ("", "void") else len(params.split(","))
+    lib = hot.load()
+    checked = 0
+    for name, n in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+        checked += 1
+    assert checked == len(declared_functions())
+
+
+def test_null_handles_are_rejected_without_a_device():
+    """Argument marshalling of the residency and wait-limit calls: a NULL
+    scene or server is refused with MPM_ERR_INVALID_ARG before any CUDA call."""
+    lib = hot.load()
+    invalid = 1
+    assert lib.mpm_scene_park(None) == invalid
+    assert lib.mpm_scene_unpark(None) == invalid
+    assert lib.mpm_set_wait_limit(None, ctypes.c_int64(1 << 40)) == invalid
+    p, b = ctypes.c_int32(7), ctypes.c_int64(7)
+    assert lib.mpm_scene_residency(None, ctypes.byref(p), ctypes.byref(b)) == invalid
+    w = [ctypes.c_int64(7) for _ in range(5)]
+    assert lib.mpm_server_residency(None, *[ctypes.byref(x) for x in w]) == invalid
+    assert p.value == 7 and b.value == 7 and all(x.value == 7 for x in w)
